@@ -1,0 +1,170 @@
+/*
+ * pw.h -- C ABI of the GB300 Piacsek-Williams (PW) advection library.
+ *
+ * The library computes the PW advection source terms (su, sv, sw) of the
+ * staggered Arakawa-C winds (u, v, w) on sm_103a GPUs. Paper: N. Brown,
+ * "Accelerating advection for atmospheric modelling on Xilinx and Intel
+ * FPGAs", arXiv:2107.13500; the su stencil is its Listing 1 (Sec. II-A),
+ * the operation count its Sec. III.
+ *
+ * Conventions for every entry point:
+ *  - Layout. A field of an nx x ny x nz domain is stored x fastest as
+ *    f[k*sz + j*sy + i] with i = 0..nx+1, j = 0..ny+1 (0 and n+1 are a
+ *    one-cell halo) and k = 0..nz-1 (the paper's level k+1; no vertical
+ *    halo). sy >= nx+2 and sz >= sy*(ny+2) are element strides. Device
+ *    buffers must start on a 16-byte boundary and sy, sz must be multiples
+ *    of 16 bytes (TMA tile loads); rows padded to 32 bytes satisfy this.
+ *  - Ownership. The caller owns every buffer. The library allocates no
+ *    device memory on any compute path.
+ *  - Asynchrony. Compute calls enqueue work on `stream` (a cudaStream_t;
+ *    NULL = the legacy default stream) and return before it finishes.
+ *  - Outputs. Only interior cells (i = 1..nx, j = 1..ny, all k) are written;
+ *    output halo cells are never touched. Outputs may not overlap inputs or
+ *    each other.
+ *  - Inputs. Halo cells of inputs must hold valid values (periodic copies
+ *    from pw_fill_periodic_halo, or boundary data the caller supplies).
+ *  - Errors. Every call returns PW_OK (0) or a negative PW_E* code, and
+ *    pw_last_error() returns a message for the last failure in the calling
+ *    thread. A failed validation enqueues nothing.
+ */
+#ifndef PW_H
+#define PW_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PW_OK 0
+#define PW_EINVAL (-1)        /* bad size, halo, stride, alignment or option */
+#define PW_ENULL (-2)         /* a required pointer is NULL */
+#define PW_EALIAS (-3)        /* an output overlaps an input or another output */
+#define PW_EUNSUPPORTED (-4)  /* dtype/operation combination not provided */
+#define PW_ECUDA (-5)         /* a CUDA runtime or driver call failed */
+#define PW_ETIMEOUT (-6)      /* a kernel's bounded wait expired (see pw_device_status) */
+
+typedef enum {
+    PW_F64 = 0,        /* double in, double out, native FP64 arithmetic */
+    PW_F32_SPLIT = 1,  /* float perturbations about per-level means, FP32 arithmetic */
+    PW_F64_PAIRED = 2  /* double in, double out, paired-FP32 (double-float) arithmetic */
+} pw_dtype;
+
+/* Domain shape and strides (elements). halo must be 1. */
+typedef struct {
+    int nx, ny, nz, halo;
+    long long sy, sz;
+} pw_dims;
+
+/* Stencil coefficients of Listing 1 and its companions: tcx, tcy (host
+ * scalars) and four DEVICE arrays of length nz (level k at index k-1):
+ * tzc1/tzc2 weight the lower/upper vertical flux of su and sv, tzd1/tzd2
+ * those of sw. pw_make_coeffs fills them on the host. */
+typedef struct {
+    double tcx, tcy;
+    const double *tzc1, *tzc2, *tzd1, *tzd2;
+} pw_coeffs;
+
+/* Number of floats per level in the PW_F32_SPLIT table (see pw_make_split_table). */
+#define PW_SPLIT_NCOEF 32
+
+/*
+ * pw_make_coeffs -- host FP64 coefficients (no GPU work).
+ *   tc2_host[0] = tcx = 0.25/dx, tc2_host[1] = tcy = 0.25/dy.
+ *   tz4_host (4*nz doubles) = tzc1 | tzc2 | tzd1 | tzd2, each nz long:
+ *     z(1) = 0, z(k) = z(k-1) + dz(k); zn(k) = (z(k-1)+z(k))/2, zn(1) = -zn(2);
+ *     dzn(k) = zn(k+1) - zn(k);
+ *     tzc1(k) = 0.25 rho(k-1)/(rhon(k) dz(k)),  tzc2(k) = 0.25 rho(k)/(rhon(k) dz(k));
+ *     tzd1(k) = 0.25 rhon(k)/(rho(k) dzn(k)),   tzd2(k) = 0.25 rhon(k+1)/(rho(k) dzn(k));
+ *   unused entries (tzc at level 1, tzd at levels 1 and nz) are 0.
+ * The paper uses these coefficients in Listing 1 without defining them;
+ * this is the flux-form reading on a stretched, density-weighted grid.
+ * dz: host, nz entries (dz[0] unused). rho (w levels) and rhon (u levels):
+ * host, nz entries, or NULL for 1. Errors: PW_ENULL, PW_EINVAL (nz < 1,
+ * dx, dy or dz(k>=2) not > 0).
+ */
+int pw_make_coeffs(int nz, double dx, double dy, const double *dz, const double *rho,
+                   const double *rhon, double *tc2_host, double *tz4_host);
+
+/*
+ * pw_fill_periodic_halo -- make a field periodic in x and y on the device:
+ * copies column nx into column 0 and column 1 into column nx+1 (every row),
+ * then row ny into row 0 and row 1 into row ny+1 (every column, so corners
+ * follow). dtype selects the element size (PW_F32_SPLIT = float, else
+ * double). Errors: PW_ENULL, PW_EINVAL, PW_ECUDA.
+ */
+int pw_fill_periodic_halo(pw_dtype dtype, void *field, const pw_dims *dims, void *stream);
+
+/*
+ * pw_advect -- the source terms of Listing 1 (su) and its two companions.
+ * For every interior column (i, j):
+ *   level 1: su = sv = sw = 0 (Listing 1 starts at k = 2);
+ *   k = 2..nz:
+ *     su = tcx[u(i-1)(u(i)+u(i-1)) - u(i+1)(u(i)+u(i+1))]
+ *        + tcy[u(j-1)(v(j-1,i)+v(j-1,i+1)) - u(j+1)(v(j,i)+v(j,i+1))]
+ *        + tzc1(k) u(k-1)(w(k-1,i)+w(k-1,i+1)) - [k<nz] tzc2(k) u(k+1)(w(k,i)+w(k,i+1))
+ *     sv = the same with x and y exchanged (u<->v, tcx<->tcy, i<->j);
+ *   k = 2..nz-1:
+ *     sw = tcx[w(i-1)(u(k,i-1)+u(k+1,i-1)) - w(i+1)(u(k,i)+u(k+1,i))]
+ *        + tcy[w(j-1)(v(k,j-1)+v(k+1,j-1)) - w(j+1)(v(k,j)+v(k+1,j))]
+ *        + tzd1(k) w(k-1)(w(k)+w(k-1)) - tzd2(k) w(k+1)(w(k)+w(k+1));
+ *   k = nz: sw = 0 (rigid lid).
+ * Unlisted indices are (k, j, i). All of u, v, w, su, sv, sw share `dims`.
+ *
+ * dtype PW_F64 / PW_F64_PAIRED: u, v, w, su, sv, sw are double; split must
+ *   be NULL. PAIRED carries every value as an unevaluated sum of two floats
+ *   (about 48 significant bits); its results stay within 1e-13 of the
+ *   exact ones relative to the sum of the absolute values of the product
+ *   terms at each point, for inputs and coefficients whose magnitudes lie
+ *   in [2^-60, 2^60] (or are 0).
+ * dtype PW_F32_SPLIT: u, v, w are float perturbations u' = u - U(k) about
+ *   per-level means, su, sv, sw are float, and `split` is a DEVICE table of
+ *   PW_SPLIT_NCOEF*nz floats built by pw_make_split_table (the coefficient
+ *   arrays in `c` are then not read, but c must still be non-NULL).
+ * Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_EUNSUPPORTED, PW_ECUDA.
+ */
+int pw_advect(pw_dtype dtype, const void *u, const void *v, const void *w, const pw_coeffs *c,
+              const pw_dims *dims, const void *split, void *su, void *sv, void *sw, void *stream);
+
+/*
+ * pw_make_split_table -- host FP64 set-up for PW_F32_SPLIT (no GPU work).
+ * Given tcx, tcy, tz4_host (as from pw_make_coeffs) and the per-level means
+ * ubar, vbar, wbar (host, nz doubles each), writes table_host
+ * (PW_SPLIT_NCOEF*nz floats, level-major: entry m of level k at k*NCOEF+m).
+ * Writing u = U(k) + u' (likewise v, w), every mean x mean product of a
+ * horizontal flux difference cancels exactly, and each vertical flux
+ * difference leaves a per-level constant that is formed here in FP64 and
+ * rounded to float once; the remaining terms are linear or quadratic in the
+ * perturbations. Errors: PW_ENULL, PW_EINVAL.
+ */
+int pw_make_split_table(int nz, double tcx, double tcy, const double *tz4_host,
+                        const double *ubar, const double *vbar, const double *wbar,
+                        float *table_host);
+
+/*
+ * pw_split_field -- per-level mean and float perturbation of a double field
+ * on the device: mean[k] = average of f over the interior of level k
+ * (FP64, fixed summation order, so repeatable), fp = float(f - mean[k]) on
+ * every cell of the level including the halo. f uses dims_f (double), fp
+ * uses dims_p (float; same nx, ny, nz). mean is a DEVICE array of nz doubles.
+ * Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_ECUDA.
+ */
+int pw_split_field(const double *f, const pw_dims *dims_f, float *fp, const pw_dims *dims_p,
+                   double *mean, void *stream);
+
+/*
+ * pw_device_status -- read and clear the library's device error word on the
+ * current device (synchronises `stream`). *status receives 0, or PW_ETIMEOUT
+ * if a kernel gave up on a bounded wait since the last call (its outputs are
+ * then unspecified). Errors: PW_ENULL, PW_ECUDA.
+ */
+int pw_device_status(int *status, void *stream);
+
+/* Message for the last failing call in this thread ("" if none). */
+const char *pw_last_error(void);
+
+/* Library version string. */
+const char *pw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PW_H */

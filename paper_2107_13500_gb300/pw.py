@@ -1,0 +1,249 @@
+"""Python binding of the C ABI in include/pw.h (argument marshalling only).
+
+Every computation runs in ``libpw.so``'s CUDA kernels; this module only
+turns torch tensors into pointers, sizes and a stream handle. PyTorch
+supplies device memory and streams. There is no CPU fallback: if the
+library is not built, or no GPU is present, calls raise.
+
+Fields are torch tensors of shape ``(nz, ny + 2, sy)`` indexed ``[k, j, i]``
+(x fastest, one halo cell in x and y, rows padded so that each starts on a
+32-byte boundary); :func:`empty_field` allocates that layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+PW_OK = 0
+PW_EINVAL = -1
+PW_ENULL = -2
+PW_EALIAS = -3
+PW_EUNSUPPORTED = -4
+PW_ECUDA = -5
+PW_ETIMEOUT = -6
+
+PW_F64 = 0
+PW_F32_SPLIT = 1
+PW_F64_PAIRED = 2
+PW_SPLIT_NCOEF = 32
+
+MODES = {"f64": PW_F64, "paired": PW_F64_PAIRED, "split": PW_F32_SPLIT}
+
+# Algorithmic HBM traffic per point: read u, v, w once, write su, sv, sw once.
+BYTES_PER_POINT = {"f64": 48, "paired": 48, "split": 24}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libpw.so")
+
+
+
+class PWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("halo", ctypes.c_int),
+                ("sy", ctypes.c_longlong), ("sz", ctypes.c_longlong)]
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [("tcx", ctypes.c_double), ("tcy", ctypes.c_double),
+                ("tzc1", ctypes.c_void_p), ("tzc2", ctypes.c_void_p),
+                ("tzd1", ctypes.c_void_p), ("tzd2", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def load_library(path: str | None = None):
+    """Load libpw.so (built by ``build.build()``); raise if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libpw.so not found at {p}: run paper_2107_13500_gb300.build.build() "
+                               "(nvcc, sm_103a) first; there is no CPU fallback")
+        lib = ctypes.CDLL(p)
+        vp = ctypes.c_void_p
+        lib.pw_last_error.restype = ctypes.c_char_p
+        lib.pw_version.restype = ctypes.c_char_p
+        lib.pw_make_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp, _dp]
+        lib.pw_fill_periodic_halo.argtypes = [ctypes.c_int, vp, ctypes.POINTER(Dims), vp]
+        lib.pw_advect.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(Coeffs), ctypes.POINTER(Dims), vp,
+                                  vp, vp, vp, vp]
+        lib.pw_make_split_table.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp, _dp,
+                                            _fp]
+        lib.pw_split_field.argtypes = [vp, ctypes.POINTER(Dims), vp, ctypes.POINTER(Dims), vp, vp]
+        lib.pw_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), vp]
+        for name in ("pw_make_coeffs", "pw_fill_periodic_halo", "pw_advect", "pw_make_split_table",
+                     "pw_split_field", "pw_device_status"):
+            getattr(lib, name).restype = ctypes.c_int
+        if hasattr(lib, "pw_advect_adjoint"):
+            lib.pw_advect_adjoint.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(Coeffs),
+                                              ctypes.POINTER(Dims), vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
+            lib.pw_advect_adjoint.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != PW_OK:
+        raise PWError(rc, load_library().pw_last_error().decode())
+
+
+def version() -> str:
+    return load_library().pw_version().decode()
+
+
+# ---------------------------------------------------------------- layouts
+
+def row_stride(nx: int, elem_bytes: int) -> int:
+    per = 32 // elem_bytes
+    return ((nx + 2 + per - 1) // per) * per
+
+
+def empty_field(nx, ny, nz, dtype=None, device="cuda"):
+    import torch
+    dtype = dtype or torch.float64
+    es = torch.empty((), dtype=dtype).element_size()
+    return torch.zeros((nz, ny + 2, row_stride(nx, es)), dtype=dtype, device=device)
+
+
+def dims_of(t, nx: int, ny: int) -> Dims:
+    if t.dim() != 3 or t.stride(2) != 1:
+        raise ValueError("fields must be 3-D (nz, ny+2, sy) tensors with x contiguous")
+    nz = t.shape[0]
+    if t.shape[1] != ny + 2 or t.shape[2] < nx + 2:
+        raise ValueError(f"field shape {tuple(t.shape)} does not hold a {nx}x{ny} interior with halo")
+    return Dims(nx, ny, nz, 1, t.stride(1), t.stride(0))
+
+
+def _stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------- coefficients
+
+@dataclass
+class Coefficients:
+    """Host FP64 coefficients (from pw_make_coeffs) and their device copies."""
+    nz: int
+    tcx: float
+    tcy: float
+    tz4: np.ndarray          # (4, nz): tzc1, tzc2, tzd1, tzd2
+    dev: object = None        # torch (4, nz) float64 on the GPU
+
+    def to_device(self, device="cuda"):
+        import torch
+        if self.dev is None or str(self.dev.device) != str(torch.device(device)):
+            self.dev = torch.from_numpy(self.tz4.copy()).to(device)
+        return self
+
+    def c_struct(self) -> Coeffs:
+        if self.dev is None:
+            self.to_device()
+        d = self.dev
+        return Coeffs(self.tcx, self.tcy, d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr())
+
+    def as_dict(self):
+        return dict(tcx=self.tcx, tcy=self.tcy, tzc1=self.tz4[0], tzc2=self.tz4[1], tzd1=self.tz4[2],
+                    tzd2=self.tz4[3])
+
+
+def make_coeffs(nz, dx, dy, dz, rho=None, rhon=None) -> Coefficients:
+    lib = load_library()
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    if dz.shape != (nz,):
+        raise ValueError("dz must have nz entries")
+    rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    rhon = None if rhon is None else np.ascontiguousarray(rhon, dtype=np.float64)
+    tc = np.zeros(2)
+    tz = np.zeros((4, nz))
+    _check(lib.pw_make_coeffs(nz, float(dx), float(dy), dz.ctypes.data_as(_dp),
+                              None if rho is None else rho.ctypes.data_as(_dp),
+                              None if rhon is None else rhon.ctypes.data_as(_dp),
+                              tc.ctypes.data_as(_dp), tz.ctypes.data_as(_dp)))
+    return Coefficients(nz, float(tc[0]), float(tc[1]), tz)
+
+
+def make_split_table(coeffs: Coefficients, ubar, vbar, wbar) -> np.ndarray:
+    lib = load_library()
+    nz = coeffs.nz
+    ub, vb, wb = (np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(nz)) for m in (ubar, vbar, wbar))
+    tz = np.ascontiguousarray(coeffs.tz4)
+    out = np.zeros((nz, PW_SPLIT_NCOEF), dtype=np.float32)
+    _check(lib.pw_make_split_table(nz, coeffs.tcx, coeffs.tcy, tz.ctypes.data_as(_dp), ub.ctypes.data_as(_dp),
+                                   vb.ctypes.data_as(_dp), wb.ctypes.data_as(_dp), out.ctypes.data_as(_fp)))
+    return out
+
+
+# ---------------------------------------------------------------- compute calls
+
+def fill_periodic_halo(f, nx, ny, stream=None):
+    import torch
+    dt = PW_F32_SPLIT if f.dtype == torch.float32 else PW_F64
+    d = dims_of(f, nx, ny)
+    _check(load_library().pw_fill_periodic_halo(dt, ctypes.c_void_p(f.data_ptr()), ctypes.byref(d),
+                                                _stream_handle(stream)))
+    return f
+
+
+def advect(u, v, w, coeffs: Coefficients, nx, ny, mode="paired", split_table=None, out=None, stream=None):
+    """Source terms (su, sv, sw) of u, v, w.
+
+    mode: "f64" (native FP64), "paired" (FP64 in/out, paired-FP32
+    arithmetic) or "split" (float perturbations; ``split_table`` is the
+    device table from :func:`make_split_table`).
+    """
+    import torch
+    lib = load_library()
+    dt = MODES[mode]
+    d = dims_of(u, nx, ny)
+    for t in (v, w):
+        if t.shape != u.shape or t.stride() != u.stride() or t.dtype != u.dtype:
+            raise ValueError("u, v, w must share shape, strides and dtype")
+    if out is None:
+        out = tuple(torch.empty_strided(u.shape, u.stride(), dtype=u.dtype, device=u.device) for _ in range(3))
+    su, sv, sw = out
+    for t in out:
+        if t.shape != u.shape or t.stride() != u.stride() or t.dtype != u.dtype:
+            raise ValueError("outputs must match the inputs' layout")
+    c = coeffs.c_struct()
+    sp = None if split_table is None else ctypes.c_void_p(split_table.data_ptr())
+    _check(lib.pw_advect(dt, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                         ctypes.c_void_p(w.data_ptr()), ctypes.byref(c), ctypes.byref(d), sp,
+                         ctypes.c_void_p(su.data_ptr()), ctypes.c_void_p(sv.data_ptr()),
+                         ctypes.c_void_p(sw.data_ptr()), _stream_handle(stream)))
+    return su, sv, sw
+
+
+def split_field(f, nx, ny, out=None, mean=None, stream=None):
+    """(fp, mean): float perturbation field and per-level FP64 means of f."""
+    import torch
+    lib = load_library()
+    df = dims_of(f, nx, ny)
+    fp = out if out is not None else empty_field(nx, ny, f.shape[0], torch.float32, f.device)
+    dp = dims_of(fp, nx, ny)
+    m = mean if mean is not None else torch.empty(f.shape[0], dtype=torch.float64, device=f.device)
+    _check(lib.pw_split_field(ctypes.c_void_p(f.data_ptr()), ctypes.byref(df), ctypes.c_void_p(fp.data_ptr()),
+                              ctypes.byref(dp), ctypes.c_void_p(m.data_ptr()), _stream_handle(stream)))
+    return fp, m
+
+
+def device_status(stream=None) -> int:
+    st = ctypes.c_int(0)
+    _check(load_library().pw_device_status(ctypes.byref(st), _stream_handle(stream)))
+    return st.value

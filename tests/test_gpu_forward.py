@@ -1,0 +1,171 @@
+"""GPU parity of pw_advect against the FP64 CPU oracle, through the C ABI.
+
+Inputs come from the shared seeded generators; the oracle runs on the same
+numpy arrays the GPU receives. Sizes span several tiles with ragged edges,
+the edge cases of the method (nz = 1, 2, 3; one-column domains), the full
+16.8M-point workload, and guard-band canaries around every output.
+"""
+import numpy as np
+import pytest
+
+from helpers import TOL_F64, compare_f64, interior, to_device, to_numpy_f64
+from paper_2107_13500_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+F64_MODES = ["f64", "paired"]
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2107_13500_gb300 import build, pw
+    build.build()
+    pw.load_library()
+    return torch
+
+
+def _run(gpu, mode, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, oracle_lib=None):
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    co = oracle_lib.coeffs(nz, dx, dy, dz, rho, rhon)
+    (so, ab) = oracle_lib.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=8)
+    c = pw.make_coeffs(nz, dx, dy, dz, rho, rhon).to_device()
+    du, dv, dw = (to_device(f, nx, torch.float64) for f in (u, v, w))
+    out = pw.advect(du, dv, dw, c, nx, ny, mode=mode)
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    g = [to_numpy_f64(t, u.shape[2], nx) for t in out]
+    return g, so, ab
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
+def test_small_iid_config(gpu, oracle_lib, mode):
+    """64^3 periodic, i.i.d. U[-10,10] winds, dx = dy = 50 m, dz = 20 m."""
+    cfg = synth.config_small_iid()
+    u, v, w = cfg["fields"]()
+    g, o, a = _run(gpu, mode, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"],
+                   oracle_lib=oracle_lib)
+    compare_f64(g, o, a, cfg["nx"], cfg["ny"])
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
+@pytest.mark.parametrize("shape", [(37, 13, 5), (33, 9, 7), (100, 17, 11), (31, 7, 3)])
+def test_ragged_stretched_density(gpu, oracle_lib, mode, shape):
+    """Sizes that leave partial tiles in x and y; stretched grid with density."""
+    nx, ny, nz = shape
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=nx * 7 + ny)
+    g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 40.0, 60.0, dz, rho, rhon, oracle_lib)
+    compare_f64(g, o, a, nx, ny)
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 1), (5, 4, 2), (1, 9, 4), (9, 1, 4), (64, 8, 3)])
+def test_degenerate_shapes(gpu, oracle_lib, mode, shape):
+    """nz = 1 (nothing computed), nz = 2 (only the top level), one-column
+    domains in x or y."""
+    nx, ny, nz = shape
+    dz = synth.dz_uniform(nz, 20.0)
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=99)
+    g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 50.0, 50.0, dz, oracle_lib=oracle_lib)
+    compare_f64(g, o, a, nx, ny)
+    if nz == 1:
+        for s in g:
+            assert np.all(interior(s, nx, ny) == 0.0)
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
+def test_integer_inputs_bit_exact(gpu, oracle_lib, mode):
+    """Integer winds, dyadic coefficients: no operation of either side
+    rounds, so the GPU must equal the oracle bit for bit."""
+    nx, ny, nz = 45, 21, 9
+    u, v, w = synth.fields_integer(nx, ny, nz, seed=3)
+    g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 0.25, 0.5, synth.dz_uniform(nz, 0.5), oracle_lib=oracle_lib)
+    for gi, oi in zip(g, o):
+        np.testing.assert_array_equal(interior(gi, nx, ny), interior(oi, nx, ny))
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
+def test_full_16m_modes_config(gpu, oracle_lib, mode):
+    """The 512 x 512 x 64 workload (smooth winds, mean 5 m/s, stretched grid)
+    in the launch configuration the benchmark times, compared point by point."""
+    cfg = synth.config_16m_modes()
+    u, v, w = cfg["fields"]()
+    g, o, a = _run(gpu, mode, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"],
+                   oracle_lib=oracle_lib)
+    worst = compare_f64(g, o, a, cfg["nx"], cfg["ny"])
+    print("worst (err/A, normwise):", worst)
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
+def test_guard_bands_and_halo_untouched(gpu, oracle_lib, mode):
+    """Outputs live inside a larger buffer filled with a NaN canary: after the
+    call every cell outside the interior (halo, row padding, guard bands
+    before and after) still holds the canary bit pattern."""
+    import torch
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 35, 10, 6
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=12)
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
+    du, dv, dw = (to_device(f, nx, torch.float64) for f in (u, v, w))
+    shape = du.shape
+    n = du.numel()
+    guard = 4096
+    canary = torch.tensor([0x7FF4DEADBEEF0001], dtype=torch.int64).view(torch.float64)
+    bufs, outs = [], []
+    for _ in range(3):
+        b = torch.empty(n + 2 * guard, dtype=torch.float64, device="cuda")
+        b.view(torch.int64).fill_(int(canary.view(torch.int64)))
+        bufs.append(b)
+        outs.append(b[guard:guard + n].view(shape))
+    pw.advect(du, dv, dw, c, nx, ny, mode=mode, out=tuple(outs))
+    torch.cuda.synchronize()
+    for b in bufs:
+        bits = b.view(torch.int64).cpu().numpy()
+        mask = np.ones(bits.shape, dtype=bool)
+        inner = mask[guard:guard + n].reshape(shape)
+        inner[:, 1:ny + 1, 1:nx + 1] = False
+        assert np.all(bits[mask] == int(canary.view(torch.int64))), "a cell outside the interior was written"
+
+
+def test_periodic_halo_fill_matches_numpy(gpu):
+    """pw_fill_periodic_halo against numpy's wrap padding of the interior."""
+    import torch
+    from paper_2107_13500_gb300 import pw
+    for dt, npdt in ((torch.float64, np.float64), (torch.float32, np.float32)):
+        nx, ny, nz = 29, 11, 4
+        f = synth.empty_field(nx, ny, nz, npdt)
+        f[:, 1:ny + 1, 1:nx + 1] = synth.uniform(5, 0, nx * ny * nz, -1, 1).reshape(nz, ny, nx)
+        t = pw.empty_field(nx, ny, nz, dt)
+        t[:, :, : f.shape[2]] = torch.from_numpy(f)[:, :, : t.shape[2]]
+        pw.fill_periodic_halo(t, nx, ny)
+        torch.cuda.synchronize()
+        got = t.cpu().numpy()[:, :, : nx + 2]
+        want = np.pad(f[:, 1:ny + 1, 1:nx + 1], ((0, 0), (1, 1), (1, 1)), mode="wrap")
+        np.testing.assert_array_equal(got, want)
+
+
+def test_api_rejects_bad_arguments_on_device(gpu):
+    """Aliased outputs, misaligned pointers and bad strides fail validation
+    with the documented codes, and nothing is launched."""
+    import torch
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 16, 8, 4
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
+    u, v, w = (pw.empty_field(nx, ny, nz) for _ in range(3))
+    su, sv, sw = (pw.empty_field(nx, ny, nz) for _ in range(3))
+    with pytest.raises(pw.PWError) as e:
+        pw.advect(u, v, w, c, nx, ny, mode="f64", out=(u, sv, sw))
+    assert e.value.code == pw.PW_EALIAS
+    with pytest.raises(pw.PWError) as e:
+        pw.advect(u, v, w, c, nx, ny, mode="f64", out=(su, su, sw))
+    assert e.value.code == pw.PW_EALIAS
+    flat = torch.zeros(u.numel() + 1, dtype=torch.float64, device="cuda")
+    mis = flat[1:].view(u.shape)
+    with pytest.raises(pw.PWError) as e:
+        pw.advect(mis, v, w, c, nx, ny, mode="f64", out=(su, sv, sw))
+    assert e.value.code == pw.PW_EINVAL
+    assert pw.device_status() == 0
