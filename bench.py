@@ -1,0 +1,457 @@
+#!/usr/bin/env python3
+"""Benchmark of the PW advection hot path (su, sv, sw) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pw_advect call (all three source terms, every level) over the
+512 x 512 x 64 workload (16.8M points, smooth 8-mode winds with a 5 m/s mean
+wind and 1 % noise, dx = dy = 50 m, dz growing from 10 m by 3 % per level),
+FP64 inputs and outputs, inputs resident in HBM. The headline path is the
+FP64-accurate paired-FP32 kernel (results within 1e-13 of the FP64 oracle);
+the native-FP64 kernel and the FP32 mean+perturbation kernel are measured
+beside it, and all three again on the 1024 x 1024 x 128 (134M-point)
+workload, with their errors against the FP64 oracle.
+
+Under torchrun (N > 1) every rank runs an independent replica on its own GPU
+(the method has no exchange step inside one evaluation): value = all ranks'
+points / the slowest rank's time. ``--impl reference`` times the plain FP64
+C oracle on the host cores instead (rank 0 only).
+
+Prints ONE JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2107_13500_gb300 import synth  # noqa: E402
+
+WORKLOAD = ("pw_advect su,sv,sw 512x512x64 (16.8M points), FP64 in/out, smooth 8-mode winds "
+            "+1% noise, 5 m/s mean wind, dx=dy=50 m, stretched dz=10 m*1.03^(k-2)")
+METRIC = "GPoints/s of su,sv,sw (FP64-accurate, <=1e-13 of the FP64 oracle) and % HBM roofline"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCES = ["pw_paired.cu", "pw_pair.cuh", "pw_ring.cuh", "pw_common.cuh", "pw_kernels.cu", "pw_split.cu"]
+# Paired-FP32 algorithm, FP32/INT lane operations per point as written: 31 pair
+# sums x 8 + 28 pair products x 4 + 3 double->pair splits x 15 + 3 pair->double
+# joins x 15 (halo re-splits and address/loop work excluded).
+PAIRED_ALG_OPS_PER_POINT = 31 * 8 + 28 * 4 + 3 * 15 + 3 * 15
+# FP32/INT issue peak: 152 SMs x 128 lanes x 2.07 GHz (maximum SM clock).
+ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--mode", choices=["paired", "f64", "split"], default="paired",
+                   help="arithmetic of the headline path")
+    p.add_argument("--no-extras", action="store_true", help="skip the 134M-point comparison and the CPU baseline")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2107_13500_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def time_launches(torch, fn, steps, warmup, nsets):
+    """Mean ms per call of fn(set_index), CUDA events on the current stream."""
+    for n in range(warmup):
+        fn(n % nsets)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record()
+    for n in range(steps):
+        fn(n % nsets)
+    end.record()
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / steps
+
+
+def error_stats(gpu_out, ref, ab, nx, ny):
+    out = {}
+    for name, g, o, a in zip(("su", "sv", "sw"), gpu_out, ref, ab):
+        gi = g[:, 1:ny + 1, 1:nx + 1]
+        oi = o[:, 1:ny + 1, 1:nx + 1]
+        ai = a[:, 1:ny + 1, 1:nx + 1]
+        err = np.abs(gi - oi)
+        mo = float(np.max(np.abs(oi)))
+        out[name] = {"max_err_over_A": float(np.max(err / np.maximum(ai, 1e-300))),
+                     "max_rel": float(np.max(err)) / mo if mo else 0.0,
+                     "rms_rel": float(np.sqrt(np.mean(err ** 2)) / max(np.sqrt(np.mean(oi ** 2)), 1e-300))}
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """The plain FP64 C oracle on the host cores, on this arm's workload.
+
+    Each step evaluates the full 512x512x64 domain when K + W such steps fit
+    in about 100 s; otherwise each step evaluates a y-slab of the domain (all
+    levels and columns, fewer rows) sized to that budget. GPoints/s counts
+    the points actually evaluated.
+    """
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_oracle()
+    cfg = synth.config_16m_modes()
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    u, v, w = cfg["fields"]()
+    co = oracle.coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"])
+    cores = os.cpu_count() or 1
+    out = tuple(np.zeros_like(u) for _ in range(3))
+    t0 = time.perf_counter()
+    oracle.advect(u, v, w, co, nx, ny, nthreads=cores, out=out)
+    t_full = time.perf_counter() - t0
+    budget = 100.0 / max(args.steps + args.warmup, 1)
+    rows = ny
+    if t_full > budget:
+        rows = max(4, min(ny, int(ny * budget / t_full)))
+        u, v, w = (np.ascontiguousarray(f[:, : rows + 2, :]) for f in (u, v, w))
+        out = tuple(np.zeros_like(u) for _ in range(3))
+    for _ in range(max(args.warmup, 0)):
+        oracle.advect(u, v, w, co, nx, rows, nthreads=cores, out=out)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.advect(u, v, w, co, nx, rows, nthreads=cores, out=out)
+    dt = (time.perf_counter() - t0) / args.steps
+    pts = nx * rows * nz
+    val = pts / dt / 1e9
+    sample = (f"{nx}x{rows}x{nz} {'(full domain)' if rows == ny else 'y-slab of the domain'} per step, "
+              f"{args.steps} steps, OpenMP {cores} threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GPoints/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "nz": nz, "rows_per_step": rows},
+        "cpu_baseline": {"value": val, "unit": "GPoints/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GPoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def cpu_baseline(u, v, w, co, nx, ny, nz):
+    """Oracle on the host cores: repeated full-domain calls for ~10-30 s."""
+    import oracle
+    cores = os.cpu_count() or 1
+    out = tuple(np.zeros_like(u) for _ in range(3))
+    t0 = time.perf_counter()
+    oracle.advect(u, v, w, co, nx, ny, nthreads=cores, out=out)
+    one = time.perf_counter() - t0
+    reps = int(max(1, min(200, 12.0 / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.advect(u, v, w, co, nx, ny, nthreads=cores, out=out)
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": nx * ny * nz / dt / 1e9, "unit": "GPoints/s", "cores": cores, "kind": "oracle",
+            "sample": f"{reps} full {nx}x{ny}x{nz} evaluations ({reps * dt:.1f} s), OpenMP {cores} threads"}
+
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_2107_13500_gb300 import build, pw
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    build.build()
+    pw.load_library()
+
+    cfg = synth.config_16m_modes()
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    pts = nx * ny * nz
+    u_np, v_np, w_np = cfg["fields"]()
+    c = pw.make_coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"]).to_device()
+    mode = args.mode
+    tdt = torch.float32 if mode == "split" else torch.float64
+    nsets = 2
+    sets = []
+    table = None
+    for _ in range(nsets):
+        fin = [torch.from_numpy(a).cuda() for a in (u_np, v_np, w_np)]
+        if mode == "split":
+            fin, means = zip(*(pw.split_field(t, nx, ny) for t in fin))
+            if table is None:
+                table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
+        fout = [torch.empty_like(fin[0]) for _ in range(3)]
+        sets.append((list(fin), fout))
+    stream = torch.cuda.current_stream()
+
+    def step(n):
+        fi, fo = sets[n]
+        pw.advect(*fi, c, nx, ny, mode=mode, out=tuple(fo), split_table=table, stream=stream)
+
+    # warm-up + timed region (device time, inputs resident)
+    sampler = ClockSampler(local)
+    for n in range(args.warmup):
+        step(n % nsets)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for n in range(args.steps):
+        step(n % nsets)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    status = pw.device_status()
+    if status != 0:
+        raise SystemExit(f"kernel reported device status {status}")
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * pts / (ms * 1e-3) / 1e9
+
+    # end to end through the public API: pinned host inputs -> device -> pw_advect -> host outputs
+    host_in = [torch.from_numpy(a).pin_memory() for a in (u_np, v_np, w_np)]
+    host_out = [torch.empty(u_np.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
+    dev_in = [torch.empty(u_np.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
+    dev_out = [torch.empty_like(dev_in[0]) for _ in range(3)]
+    e2e_mode = mode if mode != "split" else "paired"
+
+    def e2e_step(_):
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        pw.advect(*dev_in, c, nx, ny, mode=e2e_mode, out=tuple(dev_out), stream=stream)
+        for h, d in zip(host_out, dev_out):
+            h.copy_(d, non_blocking=True)
+
+    e2e_steps = max(5, min(args.steps // 10, 200))
+    e2e_ms = time_launches(torch, e2e_step, e2e_steps, 3, 1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    field_bytes = u_np.nbytes
+    e2e = {"value": world * pts / (e2e_ms * 1e-3) / 1e9, "unit": "GPoints/s",
+           "h2d_bytes_per_step": 3 * field_bytes, "d2h_bytes_per_step": 3 * field_bytes,
+           "ms_per_step": e2e_ms, "path": f"pinned host -> H2D -> pw_advect({e2e_mode}) -> D2H, one stream"}
+
+    peak, peak_kind = measured_peaks()
+    bpp = pw.BYTES_PER_POINT[mode]
+    achieved = bpp * pts / (ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        with open(PROFILE_TRAFFIC) as fh:
+            prof = json.load(fh)
+        ent = prof.get(mode)
+        if ent and ent.get("source_hash") == kernel_source_hash():
+            traffic = ent.get("bytes_per_launch")
+    hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+           "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpp * pts,
+           "kernel": f"pw_advect[{mode}] (one launch per step)"}
+    if mode == "paired":
+        tops = PAIRED_ALG_OPS_PER_POINT * pts / (ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tops, "peak": ALU_PEAK_TOPS, "unit": "TOP/s",
+                    "frac": tops / ALU_PEAK_TOPS, "traffic": traffic,
+                    "peak_kind": "derived: 152 SMs x 128 FP32/INT lanes x 2.07 GHz",
+                    "algorithmic_ops_per_point": PAIRED_ALG_OPS_PER_POINT,
+                    "kernel": "pw_advect[paired] (one launch per step)", "hbm": hbm}
+    else:
+        roofline = hbm
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GPoints/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"paired": "f32x2", "f64": "f64", "split": "f32"}[mode],
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nx": nx, "ny": ny, "nz": nz, "points_per_gpu": pts,
+                   "mode": mode, "io_dtype": "f64" if mode != "split" else "f32+f64 level means",
+                   "l2": "per-step working set 3x135 MB in + 3x135 MB out > 129 MB L2; 2 buffer sets rotate",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline,
+        "hbm_roofline_frac": achieved / peak,
+        "e2e": e2e,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+
+    if rank == 0 and world == 1 and not args.no_extras:
+        import oracle
+        oracle.build_oracle()
+        co = oracle.coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"])
+        ref, ab = oracle.advect(u_np, v_np, w_np, co, nx, ny, want_abs=True, nthreads=os.cpu_count() or 1)
+        # errors of this run's outputs (last timed step) against the oracle
+        last = sets[(args.steps - 1) % nsets][1]
+        gout = [t.double().cpu().numpy() for t in last]
+        line["error_vs_oracle"] = error_stats(gout, ref, ab, nx, ny)
+        line["cpu_baseline"] = cpu_baseline(u_np, v_np, w_np, co, nx, ny, nz)
+        line["modes"] = extra_modes(torch, pw, oracle, args, sets, c, cfg, ref, ab, peak)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def extra_modes(torch, pw, oracle, args, sets16, c16, cfg16, ref16, ab16, peak):
+    """The other arithmetic modes at 16.8M points, and all three at 134M
+    points (FP32 vs FP64 on the same GPU), each with its error against the
+    FP64 oracle."""
+    res = {}
+    steps = max(10, min(args.steps // 10, 300))
+    nx, ny, nz = cfg16["nx"], cfg16["ny"], cfg16["nz"]
+    fin16 = [sets16[0][0][n].double() if sets16[0][0][n].dtype != torch.float64 else sets16[0][0][n]
+             for n in range(3)]
+
+    def measure(label, fin, c, nx, ny, nz, mode, table, ref, ab):
+        fout = [torch.empty_like(fin[0]) for _ in range(3)]
+        ms = time_launches(torch, lambda _: pw.advect(*fin, c, nx, ny, mode=mode, out=tuple(fout),
+                                                       split_table=table), steps, 3, 1)
+        pts = nx * ny * nz
+        bpp = pw.BYTES_PER_POINT[mode]
+        g = [t.double().cpu().numpy() for t in fout]
+        res[label] = {"GPoints_s": pts / (ms * 1e-3) / 1e9, "ms": ms, "GB_s": bpp * pts / (ms * 1e-3) / 1e9,
+                      "hbm_frac": bpp * pts / (ms * 1e-3) / 1e9 / peak, "bytes_per_point": bpp,
+                      "error_vs_oracle": error_stats(g, ref, ab, nx, ny)}
+
+    if sets16[0][0][0].dtype == torch.float64:
+        for mode in ("f64", "paired", "split"):
+            if mode == "split":
+                fp, means = zip(*(pw.split_field(t, nx, ny) for t in fin16))
+                table = torch.from_numpy(pw.make_split_table(c16, *(m.cpu().numpy() for m in means))).cuda()
+                measure("16m_split", list(fp), c16, nx, ny, nz, "split", table, ref16, ab16)
+            else:
+                measure(f"16m_{mode}", fin16, c16, nx, ny, nz, mode, None, ref16, ab16)
+    # 1024 x 1024 x 128 with i.i.d. winds and uniform 20 m levels
+    cfg = synth.config_134m_iid()
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    u, v, w = cfg["fields"]()
+    co = oracle.coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"])
+    ref, ab = oracle.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=os.cpu_count() or 1)
+    c = pw.make_coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"]).to_device()
+    fin = [torch.from_numpy(a).cuda() for a in (u, v, w)]
+    del u, v, w
+    for mode in ("f64", "paired"):
+        measure(f"134m_{mode}", fin, c, nx, ny, nz, mode, None, ref, ab)
+    fp, means = zip(*(pw.split_field(t, nx, ny) for t in fin))
+    table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
+    del fin
+    measure("134m_split", list(fp), c, nx, ny, nz, "split", table, ref, ab)
+    r = res
+    r["fp32_split_speedup_over_paired_134m"] = r["134m_split"]["GPoints_s"] / r["134m_paired"]["GPoints_s"]
+    r["fp32_split_speedup_over_f64_134m"] = r["134m_split"]["GPoints_s"] / r["134m_f64"]["GPoints_s"]
+    return res
+
+
+if __name__ == "__main__":
+    main()

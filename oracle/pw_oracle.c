@@ -133,13 +133,13 @@ void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
                 }
                 AT(su, k, j, i) = s;
                 if (asu) {
-                    a = absd(tcx) * (absd(AT(u, k, j, i - 1)) * absd(AT(u, k, j, i) + AT(u, k, j, i - 1))
-                                     + absd(AT(u, k, j, i + 1)) * absd(AT(u, k, j, i) + AT(u, k, j, i + 1)));
-                    a += absd(tcy) * (absd(AT(u, k, j - 1, i)) * absd(AT(v, k, j - 1, i) + AT(v, k, j - 1, i + 1))
-                                      + absd(AT(u, k, j + 1, i)) * absd(AT(v, k, j, i) + AT(v, k, j, i + 1)));
-                    a += absd(tzc1[k]) * absd(AT(u, k - 1, j, i)) * absd(AT(w, k - 1, j, i) + AT(w, k - 1, j, i + 1));
+                    a = absd(tcx) * (absd(AT(u, k, j, i - 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k, j, i - 1)))
+                                     + absd(AT(u, k, j, i + 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k, j, i + 1))));
+                    a += absd(tcy) * (absd(AT(u, k, j - 1, i)) * (absd(AT(v, k, j - 1, i)) + absd(AT(v, k, j - 1, i + 1)))
+                                      + absd(AT(u, k, j + 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k, j, i + 1))));
+                    a += absd(tzc1[k]) * absd(AT(u, k - 1, j, i)) * (absd(AT(w, k - 1, j, i)) + absd(AT(w, k - 1, j, i + 1)));
                     if (!top)
-                        a += absd(tzc2[k]) * absd(AT(u, k + 1, j, i)) * absd(AT(w, k, j, i) + AT(w, k, j, i + 1));
+                        a += absd(tzc2[k]) * absd(AT(u, k + 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k, j, i + 1)));
                     AT(asu, k, j, i) = a;
                 }
 
@@ -156,13 +156,13 @@ void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
                 }
                 AT(sv, k, j, i) = s;
                 if (asv) {
-                    a = absd(tcy) * (absd(AT(v, k, j - 1, i)) * absd(AT(v, k, j, i) + AT(v, k, j - 1, i))
-                                     + absd(AT(v, k, j + 1, i)) * absd(AT(v, k, j, i) + AT(v, k, j + 1, i)));
-                    a += absd(tcx) * (absd(AT(v, k, j, i - 1)) * absd(AT(u, k, j, i - 1) + AT(u, k, j + 1, i - 1))
-                                      + absd(AT(v, k, j, i + 1)) * absd(AT(u, k, j, i) + AT(u, k, j + 1, i)));
-                    a += absd(tzc1[k]) * absd(AT(v, k - 1, j, i)) * absd(AT(w, k - 1, j, i) + AT(w, k - 1, j + 1, i));
+                    a = absd(tcy) * (absd(AT(v, k, j - 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k, j - 1, i)))
+                                     + absd(AT(v, k, j + 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k, j + 1, i))));
+                    a += absd(tcx) * (absd(AT(v, k, j, i - 1)) * (absd(AT(u, k, j, i - 1)) + absd(AT(u, k, j + 1, i - 1)))
+                                      + absd(AT(v, k, j, i + 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k, j + 1, i))));
+                    a += absd(tzc1[k]) * absd(AT(v, k - 1, j, i)) * (absd(AT(w, k - 1, j, i)) + absd(AT(w, k - 1, j + 1, i)));
                     if (!top)
-                        a += absd(tzc2[k]) * absd(AT(v, k + 1, j, i)) * absd(AT(w, k, j, i) + AT(w, k, j + 1, i));
+                        a += absd(tzc2[k]) * absd(AT(v, k + 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k, j + 1, i)));
                     AT(asv, k, j, i) = a;
                 }
 
@@ -178,12 +178,12 @@ void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
                           - tzd2[k] * AT(w, k + 1, j, i) * (AT(w, k, j, i) + AT(w, k + 1, j, i));
                     AT(sw, k, j, i) = s;
                     if (asw) {
-                        a = absd(tcx) * (absd(AT(w, k, j, i - 1)) * absd(AT(u, k, j, i - 1) + AT(u, k + 1, j, i - 1))
-                                         + absd(AT(w, k, j, i + 1)) * absd(AT(u, k, j, i) + AT(u, k + 1, j, i)));
-                        a += absd(tcy) * (absd(AT(w, k, j - 1, i)) * absd(AT(v, k, j - 1, i) + AT(v, k + 1, j - 1, i))
-                                          + absd(AT(w, k, j + 1, i)) * absd(AT(v, k, j, i) + AT(v, k + 1, j, i)));
-                        a += absd(tzd1[k]) * absd(AT(w, k - 1, j, i)) * absd(AT(w, k, j, i) + AT(w, k - 1, j, i));
-                        a += absd(tzd2[k]) * absd(AT(w, k + 1, j, i)) * absd(AT(w, k, j, i) + AT(w, k + 1, j, i));
+                        a = absd(tcx) * (absd(AT(w, k, j, i - 1)) * (absd(AT(u, k, j, i - 1)) + absd(AT(u, k + 1, j, i - 1)))
+                                         + absd(AT(w, k, j, i + 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k + 1, j, i))));
+                        a += absd(tcy) * (absd(AT(w, k, j - 1, i)) * (absd(AT(v, k, j - 1, i)) + absd(AT(v, k + 1, j - 1, i)))
+                                          + absd(AT(w, k, j + 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k + 1, j, i))));
+                        a += absd(tzd1[k]) * absd(AT(w, k - 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k - 1, j, i)));
+                        a += absd(tzd2[k]) * absd(AT(w, k + 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k + 1, j, i)));
                         AT(asw, k, j, i) = a;
                     }
                 } else {

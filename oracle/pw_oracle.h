@@ -34,8 +34,9 @@ int pwo_coeffs(int nz, double dx, double dy, const double *dz,
 /* Source terms su, sv, sw of Listing 1 (su) and its two companions (sv, sw).
  * Writes the interior i=1..nx, j=1..ny, every k; halo cells are untouched.
  * If asu/asv/asw are non-NULL they receive, per point, the sum of the
- * absolute values of every product term of that point (the scale against
- * which rounding error is measured). nthreads <= 0 means one thread. */
+ * absolute values of the monomials c*x*y of the bilinear form at that point
+ * (each flux c*x*(y+z) contributes |c||x|(|y|+|z|)): the scale against which
+ * rounding error is measured. nthreads <= 0 means one thread. */
 void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
                 const double *u, const double *v, const double *w,
                 double tcx, double tcy,

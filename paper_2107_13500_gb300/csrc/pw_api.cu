@@ -241,6 +241,7 @@ extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const voi
         if ((rc = check_ptr(ptrs[n], names[n], who))) return rc;
     if (dtype == PW_F32_SPLIT) {
         if (!split) return fail(PW_ENULL, "%s: PW_F32_SPLIT needs the split table", who);
+        if (((uintptr_t)split) % 16 != 0) return fail(PW_EINVAL, "%s: split table is not 16-byte aligned", who);
     } else {
         if (split) return fail(PW_EINVAL, "%s: split must be NULL unless dtype is PW_F32_SPLIT", who);
         if (!c->tzc1 || !c->tzc2 || !c->tzd1 || !c->tzd2)

@@ -17,6 +17,22 @@ constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 // Bit set in the device status word when a bounded wait expired.
 constexpr unsigned int kStatusTimeout = 1u;
 
+namespace {
+// Device status word of this translation unit (each kernel .cu file has its
+// own copy; the library ORs them when the host asks).
+__device__ unsigned int tu_status;
+
+// Copy this unit's status word to the host and clear it (ordered on st).
+__host__ inline cudaError_t read_and_clear_tu_status(unsigned int* out, cudaStream_t st) {
+    const unsigned int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbolAsync(out, tu_status, sizeof(unsigned int), 0, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbolAsync(tu_status, &zero, sizeof(unsigned int), 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+}  // namespace
+
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -41,7 +41,9 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, float* fp, long long psy,
                                long long psz, int nx, int ny, int nz, double* mean, cudaStream_t st);
 
-// Read and clear the device status word (synchronises st).
+// Read and clear the device status words of every kernel unit (synchronises st).
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st);
+cudaError_t read_and_clear_status_paired(unsigned int* status, cudaStream_t st);
+cudaError_t read_and_clear_status_split(unsigned int* status, cudaStream_t st);
 
 }  // namespace pw

@@ -16,10 +16,6 @@
 
 namespace pw {
 
-// The library's device status word (bit kStatusTimeout: a bounded wait
-// expired). Read and cleared by read_and_clear_status.
-__device__ unsigned int g_status;
-
 // ---------------------------------------------------------------------------
 // Native FP64 forward kernel.
 
@@ -143,7 +139,7 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
         }
     }
     if (abort && tid == 0) {
-        atomicOr(&g_status, kStatusTimeout);
+        atomicOr(&tu_status, kStatusTimeout);
         // let every copy still in flight land before the CTA exits
         for (int lev = (issued > S ? issued - S : 0); lev < issued; ++lev) (void)ring.wait(lev);
     }
@@ -246,12 +242,12 @@ cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, fl
 // ---------------------------------------------------------------------------
 
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st) {
-    unsigned int zero = 0;
-    cudaError_t e = cudaMemcpyFromSymbolAsync(status, g_status, sizeof(unsigned int), 0, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyToSymbolAsync(g_status, &zero, sizeof(unsigned int), 0, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(st);
+    unsigned int parts[3] = {0, 0, 0};
+    cudaError_t e = read_and_clear_tu_status(&parts[0], st);
+    if (e == cudaSuccess) e = read_and_clear_status_paired(&parts[1], st);
+    if (e == cudaSuccess) e = read_and_clear_status_split(&parts[2], st);
+    *status = parts[0] | parts[1] | parts[2];
+    return e;
 }
 
 }  // namespace pw

@@ -1,0 +1,91 @@
+// pw_pair.cuh -- paired-FP32 ("double-float") arithmetic on sm_103a.
+//
+// A value is carried as an unevaluated sum h + l of two floats (about 48
+// significant bits). Sums use Knuth's TwoSum (TAOCP vol. 2, 4.2.2) on the
+// high parts, products the FMA form of Dekker's exact product (Dekker 1971):
+// p = a*b, e = fma(a, b, -p) gives a*b = p + e exactly. Pairs are kept
+// unnormalised ("sloppy" double-float): the low-part arithmetic rounds in
+// FP32, so every operation's error is at most a few units of 2^-48 of the
+// magnitudes of its operands -- the scale against which the library states
+// its accuracy (the sum of the absolute product terms at a point).
+//
+// Conversions between double and pairs use integer bit operations only:
+// on sm_103a a conversion to or from FP64 issues on the FP64 pipe (about two
+// per clock per SM), which would cap the kernel far below the memory bound.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pw {
+
+struct pf {
+    float h, l;
+};
+
+__device__ __forceinline__ pf two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return {s, e};
+}
+
+__device__ __forceinline__ pf padd(pf a, pf b) {
+    pf s = two_sum(a.h, b.h);
+    s.l += a.l + b.l;
+    return s;
+}
+
+__device__ __forceinline__ pf psub(pf a, pf b) {
+    pf s = two_sum(a.h, -b.h);
+    s.l += a.l - b.l;
+    return s;
+}
+
+__device__ __forceinline__ pf pmul(pf a, pf b) {
+    const float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return {p, e};
+}
+
+// Split a double into (h, l): h = d rounded to 24 significant bits (ties
+// away from zero), l = float(d - h). |d - (h + l)| <= 2^-48 |d|. Valid for
+// 2^-74 <= |d| < 2^128; zero and smaller magnitudes give (0, 0).
+__device__ __forceinline__ pf split_double(double d) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+    const unsigned hw = static_cast<unsigned>(b >> 32);
+    // +2^28 in the low word rounds the 53-bit significand to 24 bits; the
+    // high-word term moves the exponent bias from 1023 to 127 (896 << 20).
+    const unsigned long long r = b + 0xC800000010000000ull;
+    const unsigned t = static_cast<unsigned>(r >> 32);
+    const unsigned lw = static_cast<unsigned>(r);
+    const unsigned hb = __funnelshift_l(lw, t, 3) | (t & 0x80000000u);
+    // The 29 bits rounding removed, as a signed count of d's last-bit unit.
+    const int rem = static_cast<int>(lw & 0x1FFFFFFFu) - 0x10000000;
+    const unsigned ex = hw & 0x7FF00000u;
+    // +-2^(E - 1075) (E = d's biased exponent): the weight of d's last bit.
+    const unsigned sb = ((ex - (948u << 20)) << 3) | (hw & 0x80000000u);
+    const float hi = __uint_as_float(hb);
+    const float lo = __int2float_rn(rem) * __uint_as_float(sb);
+    const bool tiny = ex < (949u << 20);
+    return {tiny ? 0.0f : hi, tiny ? 0.0f : lo};
+}
+
+// Exact float -> double by bit operations (normal floats and zero).
+__device__ __forceinline__ double float_bits_to_double(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned mag = b & 0x7FFFFFFFu;
+    const unsigned sign = b & 0x80000000u;
+    const unsigned hi = mag ? (((mag >> 3) + (896u << 20)) | sign) : sign;
+    const unsigned lo = b << 29;
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(lo));
+}
+
+// h + l rounded once to double (one FP64 add).
+__device__ __forceinline__ double pair_to_double(pf a) {
+    return float_bits_to_double(a.h) + float_bits_to_double(a.l);
+}
+
+}  // namespace pw

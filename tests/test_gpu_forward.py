@@ -101,6 +101,18 @@ def test_full_16m_modes_config(gpu, oracle_lib, mode):
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
+def test_full_134m_iid_config(gpu, oracle_lib, mode):
+    """1024 x 1024 x 128 with i.i.d. U[-10,10] winds (134M points, 1.1 GB per
+    field), compared point by point."""
+    cfg = synth.config_134m_iid()
+    u, v, w = cfg["fields"]()
+    g, o, a = _run(gpu, mode, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"],
+                   oracle_lib=oracle_lib)
+    del u, v, w
+    print("worst (err/A, normwise):", compare_f64(g, o, a, cfg["nx"], cfg["ny"]))
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
 def test_guard_bands_and_halo_untouched(gpu, oracle_lib, mode):
     """Outputs live inside a larger buffer filled with a NaN canary: after the
     call every cell outside the interior (halo, row padding, guard bands

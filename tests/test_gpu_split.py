@@ -1,0 +1,114 @@
+"""GPU checks of the FP32 mean+perturbation path (PW_F32_SPLIT) against the
+FP64 oracle on the original FP64 fields, and of pw_split_field.
+
+Tolerance (derived): every float operation of the split form rounds a
+quantity built from the level means and the perturbations, so its error is
+at most 2^-24 of a product of |U(k)| + |u'|-type magnitudes. Summing over
+the terms, |gpu - oracle| <= 64 * 2^-24 * A' per point, where A' is the
+oracle's sum of absolute product terms evaluated on the nonnegative fields
+|U(k)| + |u'| (likewise v, w). A' >= A; the two differ where a full wind
+value is near zero while its level mean is not, which is exactly where the
+split form rounds mean-sized quantities.
+"""
+import numpy as np
+import pytest
+
+from helpers import TOL_SPLIT_ELEM, interior, to_device
+from paper_2107_13500_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2107_13500_gb300 import build, pw
+    build.build()
+    pw.load_library()
+    return torch
+
+
+def _split_run(torch, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None):
+    from paper_2107_13500_gb300 import pw
+    c = pw.make_coeffs(nz, dx, dy, dz, rho, rhon).to_device()
+    dev = [to_device(f, nx, torch.float64) for f in (u, v, w)]
+    fp, means = zip(*(pw.split_field(t, nx, ny) for t in dev))
+    table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
+    out = pw.advect(*fp, c, nx, ny, mode="split", split_table=table)
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    return [t.double().cpu().numpy() for t in out], [m.cpu().numpy() for m in means], fp
+
+
+def _check(gpu_out, ref, ab, nx, ny):
+    stats = {}
+    for name, g, o, a in zip(("su", "sv", "sw"), gpu_out, ref, ab):
+        gi, oi, ai = interior(g, nx, ny), interior(o, nx, ny), interior(a, nx, ny)
+        err = np.abs(gi - oi)
+        assert np.all(np.isfinite(gi))
+        assert np.all(err <= TOL_SPLIT_ELEM * ai), f"{name}: max err/A {np.max(err / np.maximum(ai, 1e-300)):.3e}"
+        mo = np.max(np.abs(oi))
+        stats[name] = dict(max_rel=float(np.max(err) / mo) if mo else 0.0,
+                           rms_rel=float(np.sqrt(np.mean(err ** 2)) / max(np.sqrt(np.mean(oi ** 2)), 1e-300)))
+    return stats
+
+
+def split_scale(oracle_lib, fields, means, co, nx, ny):
+    """A' of the module docstring: absolute product terms on |mean| + |perturbation|."""
+    mags = [np.abs(m)[:, None, None] + np.abs(f - m[:, None, None]) for f, m in zip(fields, means)]
+    _, ab = oracle_lib.advect(*mags, co, nx, ny, want_abs=True, nthreads=8)
+    return ab
+
+
+def _case(gpu, oracle_lib, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None):
+    co = oracle_lib.coeffs(nz, dx, dy, dz, rho, rhon)
+    ref = oracle_lib.advect(u, v, w, co, nx, ny, nthreads=8)
+    g, means, _ = _split_run(gpu, u, v, w, nx, ny, nz, dx, dy, dz, rho, rhon)
+    ab = split_scale(oracle_lib, (u, v, w), means, co, nx, ny)
+    return _check(g, ref, ab, nx, ny)
+
+
+def test_split_small_iid(gpu, oracle_lib):
+    cfg = synth.config_small_iid()
+    u, v, w = cfg["fields"]()
+    print(_case(gpu, oracle_lib, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"]))
+
+
+@pytest.mark.parametrize("shape", [(37, 13, 5), (100, 17, 11), (31, 7, 3), (1, 1, 2), (5, 3, 1)])
+def test_split_ragged_modes_density(gpu, oracle_lib, shape):
+    """Smooth winds with a 5 m/s mean (where the split matters), stretched
+    grid with density, partial tiles, degenerate heights."""
+    nx, ny, nz = shape
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    u, v, w = synth.fields_modes(nx, ny, nz, 50.0, 50.0, dz, seed=nx + ny)
+    _case(gpu, oracle_lib, u, v, w, nx, ny, nz, 50.0, 50.0, dz, rho, rhon)
+
+
+def test_split_field_means_and_perturbations(gpu):
+    """pw_split_field: FP64 level means of the interior and float
+    perturbations on every cell, halo included."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 70, 33, 6
+    u, _, _ = synth.fields_modes(nx, ny, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0), seed=8)
+    t = to_device(u, nx, torch.float64)
+    fp, mean = pw.split_field(t, nx, ny)
+    torch.cuda.synchronize()
+    m = mean.cpu().numpy()
+    want = interior(u, nx, ny).mean(axis=(1, 2))
+    np.testing.assert_allclose(m, want, rtol=1e-14, atol=1e-14)
+    p = fp.cpu().numpy()[:, :, : nx + 2].astype(np.float64)
+    exact = u[:, :, : nx + 2] - m[:, None, None]
+    assert np.all(np.abs(p - exact) <= 2.0 ** -24 * np.abs(exact) + 1e-30)
+
+
+@pytest.mark.parametrize("which", ["16m_modes", "134m_iid"])
+def test_split_full_size(gpu, oracle_lib, which):
+    """Full-size workloads in the benchmark's launch configuration; reports
+    max and RMS errors relative to the FP64 oracle."""
+    cfg = synth.config_16m_modes() if which == "16m_modes" else synth.config_134m_iid()
+    u, v, w = cfg["fields"]()
+    stats = _case(gpu, oracle_lib, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"])
+    print(which, stats)

@@ -110,6 +110,21 @@ def test_level_constant_winds_give_zero(oracle_lib, stretched):
         assert np.all(_interior(s, nx, ny) == 0.0)
 
 
+def test_error_scale_bounds_result(oracle_lib):
+    """The per-point error scale (sum of |monomials|) bounds |result| by the
+    triangle inequality, equals it when every monomial has one sign (all
+    winds positive, only x self terms), and scales with degree two."""
+    nx, ny, nz = 9, 8, 7
+    c = oracle_lib.coeffs(nz, 50.0, 40.0, synth.dz_stretched(nz))
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=13)
+    s, a = oracle_lib.advect(u, v, w, c, nx, ny, want_abs=True)
+    for si, ai in zip(s, a):
+        assert np.all(np.abs(si) <= ai * (1 + 1e-15))
+    s2, a2 = oracle_lib.advect(2 * u, 2 * v, 2 * w, c, nx, ny, want_abs=True)
+    for ai, bi in zip(a, a2):
+        np.testing.assert_array_equal(4 * ai, bi)
+
+
 def test_level_one_is_not_computed(oracle_lib):
     nx, ny, nz = 6, 5, 6
     c = _coeffs(oracle_lib, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0))
