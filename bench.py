@@ -278,12 +278,12 @@ def main():
     sets = []
     table = None
     for _ in range(nsets):
-        fin = [torch.from_numpy(a).cuda() for a in (u_np, v_np, w_np)]
+        fin = [pw.field_from_numpy(a, nx) for a in (u_np, v_np, w_np)]
         if mode == "split":
             fin, means = zip(*(pw.split_field(t, nx, ny) for t in fin))
             if table is None:
                 table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
-        fout = [torch.empty_like(fin[0]) for _ in range(3)]
+        fout = [pw.field_like(fin[0]) for _ in range(3)]
         sets.append((list(fin), fout))
     stream = torch.cuda.current_stream()
 
@@ -323,8 +323,8 @@ def main():
     # end to end through the public API: pinned host inputs -> device -> pw_advect -> host outputs
     host_in = [torch.from_numpy(a).pin_memory() for a in (u_np, v_np, w_np)]
     host_out = [torch.empty(u_np.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
-    dev_in = [torch.empty(u_np.shape, dtype=torch.float64, device="cuda") for _ in range(3)]
-    dev_out = [torch.empty_like(dev_in[0]) for _ in range(3)]
+    dev_in = [pw.empty_field(nx, ny, nz) for _ in range(3)]
+    dev_out = [pw.empty_field(nx, ny, nz) for _ in range(3)]
     e2e_mode = mode if mode != "split" else "paired"
 
     def e2e_step(_):
@@ -414,7 +414,7 @@ def extra_modes(torch, pw, oracle, args, sets16, c16, cfg16, ref16, ab16, peak):
              for n in range(3)]
 
     def measure(label, fin, c, nx, ny, nz, mode, table, ref, ab):
-        fout = [torch.empty_like(fin[0]) for _ in range(3)]
+        fout = [pw.field_like(fin[0]) for _ in range(3)]
         ms = time_launches(torch, lambda _: pw.advect(*fin, c, nx, ny, mode=mode, out=tuple(fout),
                                                        split_table=table), steps, 3, 1)
         pts = nx * ny * nz
@@ -439,7 +439,7 @@ def extra_modes(torch, pw, oracle, args, sets16, c16, cfg16, ref16, ab16, peak):
     co = oracle.coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"])
     ref, ab = oracle.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=os.cpu_count() or 1)
     c = pw.make_coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"]).to_device()
-    fin = [torch.from_numpy(a).cuda() for a in (u, v, w)]
+    fin = [pw.field_from_numpy(a, nx) for a in (u, v, w)]
     del u, v, w
     for mode in ("f64", "paired"):
         measure(f"134m_{mode}", fin, c, nx, ny, nz, mode, None, ref, ab)

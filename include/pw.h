@@ -11,9 +11,13 @@
  *  - Layout. A field of an nx x ny x nz domain is stored x fastest as
  *    f[k*sz + j*sy + i] with i = 0..nx+1, j = 0..ny+1 (0 and n+1 are a
  *    one-cell halo) and k = 0..nz-1 (the paper's level k+1; no vertical
- *    halo). sy >= nx+2 and sz >= sy*(ny+2) are element strides. Device
- *    buffers must start on a 16-byte boundary and sy, sz must be multiples
- *    of 16 bytes (TMA tile loads); rows padded to 32 bytes satisfy this.
+ *    halo). sy >= nx+2 and sz >= sy*(ny+2) are element strides that must
+ *    be multiples of 16 bytes (TMA tile loads); rows padded to 32 bytes
+ *    satisfy this. Device buffers must be aligned to their element size, and
+ *    u, v, w must have the same address modulo 16 bytes. When the interior
+ *    cell i = 1 of all six fields starts on a 16-byte boundary (base address
+ *    = 16n - element size) the kernels use 16-byte vector accesses; any
+ *    other element-aligned layout takes an equivalent scalar path.
  *  - Ownership. The caller owns every buffer. The library allocates no
  *    device memory on any compute path.
  *  - Asynchrony. Compute calls enqueue work on `stream` (a cudaStream_t;
@@ -45,7 +49,8 @@ extern "C" {
 typedef enum {
     PW_F64 = 0,        /* double in, double out, native FP64 arithmetic */
     PW_F32_SPLIT = 1,  /* float perturbations about per-level means, FP32 arithmetic */
-    PW_F64_PAIRED = 2  /* double in, double out, paired-FP32 (double-float) arithmetic */
+    PW_F64_PAIRED = 2, /* double in, double out, paired-FP32 (double-float) arithmetic */
+    PW_F32 = 3         /* float in, float out, FP32 arithmetic on the full fields */
 } pw_dtype;
 
 /* Domain shape and strides (elements). halo must be 1. */
@@ -111,14 +116,17 @@ int pw_fill_periodic_halo(pw_dtype dtype, void *field, const pw_dims *dims, void
  *
  * dtype PW_F64 / PW_F64_PAIRED: u, v, w, su, sv, sw are double; split must
  *   be NULL. PAIRED carries every value as an unevaluated sum of two floats
- *   (about 48 significant bits); its results stay within 1e-13 of the
- *   exact ones relative to the sum of the absolute values of the product
- *   terms at each point, for inputs and coefficients whose magnitudes lie
- *   in [2^-60, 2^60] (or are 0).
+ *   (about 48 significant bits); its error at each point stays within 1e-13
+ *   of the sum of the absolute values of the monomials c*x*y of the formula
+ *   (each flux c*x*(y+z) counting |c||x|(|y|+|z|)), for inputs and
+ *   coefficients whose magnitudes lie in [2^-60, 2^60] (or are 0).
  * dtype PW_F32_SPLIT: u, v, w are float perturbations u' = u - U(k) about
  *   per-level means, su, sv, sw are float, and `split` is a DEVICE table of
  *   PW_SPLIT_NCOEF*nz floats built by pw_make_split_table (the coefficient
  *   arrays in `c` are then not read, but c must still be non-NULL).
+ * dtype PW_F32: u, v, w, su, sv, sw are float full fields; `split` is the
+ *   table of pw_make_split_table built with all means 0 (it then carries
+ *   only the coefficients, rounded to float).
  * Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_EUNSUPPORTED, PW_ECUDA.
  */
 int pw_advect(pw_dtype dtype, const void *u, const void *v, const void *w, const pw_coeffs *c,
@@ -151,10 +159,91 @@ int pw_split_field(const double *f, const pw_dims *dims_f, float *fp, const pw_d
                    double *mean, void *stream);
 
 /*
+ * pw_advect_adjoint -- transpose of the Jacobian of pw_advect at (u, v, w)
+ * applied to cotangents (gsu, gsv, gsw): the gradient a scalar J(su, sv, sw)
+ * passes back to the winds, as used in variational data assimilation. The
+ * forward map is quadratic (Listing 1 and its companions are sums of
+ * c*p*(q+r)), so d/dp = c*(q+r) and d/dq = d/dr = c*p; each cell gathers
+ * those derivatives times the cotangents of every output point that read it
+ * (no atomics). Only the computed cotangents count: the halo cells of gsu,
+ * gsv, gsw, their level 1, and level nz of gsw are ignored (read as 0).
+ * Results cover every cell the forward map reads, halo included
+ * (i = 0..nx+1, j = 0..ny+1, all k); accumulate != 0 adds them to gu, gv, gw,
+ * otherwise they overwrite. Cells beyond i = nx+1 (row padding) are not
+ * touched. dtype PW_F64 (double, native FP64) or PW_F32 (float). All nine
+ * fields share `dims`; u, v, w, gsu, gsv, gsw must have the same address
+ * modulo 16 bytes. Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_EUNSUPPORTED,
+ * PW_ECUDA.
+ */
+int pw_advect_adjoint(pw_dtype dtype, const void *u, const void *v, const void *w, const pw_coeffs *c,
+                      const pw_dims *dims, const void *gsu, const void *gsv, const void *gsw, void *gu, void *gv,
+                      void *gw, int accumulate, void *stream);
+
+/*
+ * pw_fold_periodic_halo -- transpose of pw_fill_periodic_halo: adds row 0
+ * into row ny and row ny+1 into row 1 (every column), then column 0 into
+ * column nx and column nx+1 into column 1 (rows 1..ny), zeroing the halo.
+ * Turns a gradient over all cells of a periodic field into the gradient over
+ * its interior. dtype selects the element size (PW_F32_SPLIT and PW_F32 =
+ * float, else double). Errors: PW_ENULL, PW_EINVAL, PW_ECUDA.
+ */
+int pw_fold_periodic_halo(pw_dtype dtype, void *field, const pw_dims *dims, void *stream);
+
+/*
+ * Batched evaluation: many independent domains of uneven sizes in ONE
+ * persistent launch. Every CTA of the launch takes work items (one tile of
+ * one domain) from an atomic counter until none are left, so small and
+ * large domains share the GPU without a tail per domain.
+ */
+typedef struct {
+    const void *u, *v, *w;  /* inputs (device) */
+    void *su, *sv, *sw;     /* outputs (device) */
+    pw_dims dims;
+    pw_coeffs coeffs;       /* device coefficient arrays of this domain */
+    const void *split;      /* PW_F32 / PW_F32_SPLIT: this domain's device table; else NULL */
+} pw_domain;
+
+/* Bytes of a batch plan for n domains (host and device copies alike). */
+size_t pw_batch_plan_bytes(int n);
+
+/* Number of kernel variants (tile shape x pipeline depth) for dtype; variant
+ * indices 0 .. count-1 are accepted by pw_make_batch_plan, 0 is the default.
+ * PW_F32 / PW_F32_SPLIT: 0 = 64x4 points per CTA, 4-level ring; 1 = 32x8;
+ * 2 = 128x2; 3 = 64x4 with a 3-level ring; 4 = 64x4 with a 6-level ring.
+ * PW_F64_PAIRED: 1 variant. PW_F64: 0 (not batched). */
+int pw_variant_count(pw_dtype dtype);
+
+/*
+ * pw_make_batch_plan -- host-only set-up of a batch (no GPU work, no
+ * allocation): validates every domain as pw_advect would, encodes its TMA
+ * descriptors and lays out the plan in plan_host (plan_bytes >=
+ * pw_batch_plan_bytes(n)). Domains are ordered tallest first. *n_items
+ * receives the number of work items. The caller copies the plan to a device
+ * buffer (64-byte aligned) and passes it to pw_advect_batched; the device
+ * buffer is also the kernel's work-queue scratch. dtype PW_F64_PAIRED,
+ * PW_F32 or PW_F32_SPLIT. Errors: PW_ENULL, PW_EINVAL, PW_EALIAS,
+ * PW_EUNSUPPORTED, PW_ECUDA (descriptor encoding).
+ */
+int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain *doms, int variant, void *plan_host,
+                       size_t plan_bytes, long long *n_items);
+
+/*
+ * pw_advect_batched -- evaluate every domain of a plan: resets the plan's
+ * work counter on `stream`, then launches one persistent kernel (CTAs = SMs x
+ * resident CTAs per SM, at most n_items). dtype and variant must be those the
+ * plan was built with (a mismatch is reported by pw_device_status as
+ * PW_EINVAL, outputs unspecified). Launches on the same plan must not overlap
+ * on the GPU (they share its counter). Capturable in a CUDA graph.
+ * Errors: PW_ENULL, PW_EINVAL, PW_EUNSUPPORTED, PW_ECUDA.
+ */
+int pw_advect_batched(pw_dtype dtype, int variant, void *plan_dev, long long n_items, void *stream);
+
+/*
  * pw_device_status -- read and clear the library's device error word on the
- * current device (synchronises `stream`). *status receives 0, or PW_ETIMEOUT
- * if a kernel gave up on a bounded wait since the last call (its outputs are
- * then unspecified). Errors: PW_ENULL, PW_ECUDA.
+ * current device (synchronises `stream`). *status receives 0, PW_ETIMEOUT if
+ * a kernel gave up on a bounded wait since the last call, or PW_EINVAL if a
+ * batched launch met a plan built for another dtype or variant (outputs of
+ * those launches are unspecified). Errors: PW_ENULL, PW_ECUDA.
  */
 int pw_device_status(int *status, void *stream);
 

@@ -3,7 +3,9 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -53,11 +55,15 @@ EncodeTiledFn get_encode_fn(cudaError_t* err) {
     return fn;
 }
 
+// The descriptor starts at the 16-byte boundary at or below the field's base
+// pointer; x coordinates of the tensor are i + xoff, xoff = elements between.
 int make_field_map(CUtensorMap* map, const void* base, int elem_bytes, const pw_dims& d, int box_x, int box_y) {
     cudaError_t e;
     EncodeTiledFn enc = get_encode_fn(&e);
     if (!enc) return cuda_fail(e, "cuTensorMapEncodeTiled lookup");
-    cuuint64_t gdim[3] = {(cuuint64_t)(d.nx + 2), (cuuint64_t)(d.ny + 2), (cuuint64_t)d.nz};
+    const int xoff = (int)(((uintptr_t)base % 16) / elem_bytes);
+    base = static_cast<const char*>(base) - (size_t)xoff * elem_bytes;
+    cuuint64_t gdim[3] = {(cuuint64_t)(d.nx + 2 + xoff), (cuuint64_t)(d.ny + 2), (cuuint64_t)d.nz};
     cuuint64_t gstride[2] = {(cuuint64_t)d.sy * elem_bytes, (cuuint64_t)d.sz * elem_bytes};
     cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1u};
     cuuint32_t estride[3] = {1u, 1u, 1u};
@@ -101,11 +107,16 @@ bool overlap(const void* a, long long na, const void* b, long long nb) {
     return pa < pb + (uintptr_t)nb && pb < pa + (uintptr_t)na;
 }
 
-int check_ptr(const void* p, const char* name, const char* who) {
+int check_ptr(const void* p, int elem_bytes, const char* name, const char* who) {
     if (!p) return fail(PW_ENULL, "%s: %s is NULL", who, name);
-    if (((uintptr_t)p) % 16 != 0) return fail(PW_EINVAL, "%s: %s is not 16-byte aligned", who, name);
+    if (((uintptr_t)p) % elem_bytes != 0)
+        return fail(PW_EINVAL, "%s: %s is not aligned to its %d-byte element", who, name, elem_bytes);
     return PW_OK;
 }
+
+int elem_size(pw_dtype d) { return (d == PW_F32_SPLIT || d == PW_F32) ? 4 : 8; }
+
+bool known_dtype(pw_dtype d) { return d == PW_F64 || d == PW_F32_SPLIT || d == PW_F64_PAIRED || d == PW_F32; }
 
 }  // namespace
 
@@ -213,9 +224,8 @@ extern "C" int pw_make_split_table(int nz, double tcx, double tcy, const double*
 
 extern "C" int pw_fill_periodic_halo(pw_dtype dtype, void* field, const pw_dims* dims, void* stream) {
     const char* who = "pw_fill_periodic_halo";
-    if (dtype != PW_F64 && dtype != PW_F32_SPLIT && dtype != PW_F64_PAIRED)
-        return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
-    const int es = dtype == PW_F32_SPLIT ? 4 : 8;
+    if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
+    const int es = elem_size(dtype);
     int rc = check_dims(dims, es, who);
     if (rc) return rc;
     if (!field) return fail(PW_ENULL, "%s: field is NULL", who);
@@ -229,21 +239,24 @@ extern "C" int pw_fill_periodic_halo(pw_dtype dtype, void* field, const pw_dims*
 extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const void* w, const pw_coeffs* c,
                          const pw_dims* dims, const void* split, void* su, void* sv, void* sw, void* stream) {
     const char* who = "pw_advect";
-    if (dtype != PW_F64 && dtype != PW_F32_SPLIT && dtype != PW_F64_PAIRED)
-        return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
-    const int es = dtype == PW_F32_SPLIT ? 4 : 8;
+    if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
+    const int es = elem_size(dtype);
     int rc = check_dims(dims, es, who);
     if (rc) return rc;
     if (!c) return fail(PW_ENULL, "%s: coeffs is NULL", who);
     const void* ptrs[6] = {u, v, w, su, sv, sw};
     const char* names[6] = {"u", "v", "w", "su", "sv", "sw"};
     for (int n = 0; n < 6; ++n)
-        if ((rc = check_ptr(ptrs[n], names[n], who))) return rc;
-    if (dtype == PW_F32_SPLIT) {
-        if (!split) return fail(PW_ENULL, "%s: PW_F32_SPLIT needs the split table", who);
+        if ((rc = check_ptr(ptrs[n], es, names[n], who))) return rc;
+    // u, v, w share one set of box coordinates, so they must sit at the same
+    // offset from a 16-byte boundary
+    if ((uintptr_t)v % 16 != (uintptr_t)u % 16 || (uintptr_t)w % 16 != (uintptr_t)u % 16)
+        return fail(PW_EINVAL, "%s: u, v and w must have the same address modulo 16 bytes", who);
+    if (dtype == PW_F32_SPLIT || dtype == PW_F32) {
+        if (!split) return fail(PW_ENULL, "%s: PW_F32_SPLIT and PW_F32 need the split table", who);
         if (((uintptr_t)split) % 16 != 0) return fail(PW_EINVAL, "%s: split table is not 16-byte aligned", who);
     } else {
-        if (split) return fail(PW_EINVAL, "%s: split must be NULL unless dtype is PW_F32_SPLIT", who);
+        if (split) return fail(PW_EINVAL, "%s: split must be NULL for FP64 dtypes", who);
         if (!c->tzc1 || !c->tzc2 || !c->tzd1 || !c->tzd2)
             return fail(PW_ENULL, "%s: coefficient arrays are required", who);
     }
@@ -269,6 +282,11 @@ extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const voi
     if ((rc = make_field_map(&mw, w, es, *dims, shp.box_x, shp.box_y))) return rc;
 
     pw::FwdArgs a;
+    a.xoff = (int)(((uintptr_t)u % 16) / es);
+    // vector loads/stores need i = 1 of every field on a 16-byte boundary
+    a.vec = 1;
+    for (int n = 0; n < 6; ++n)
+        if (((uintptr_t)ptrs[n] + es) % 16 != 0) a.vec = 0;
     a.nx = dims->nx;
     a.ny = dims->ny;
     a.nz = dims->nz;
@@ -320,6 +338,185 @@ extern "C" int pw_device_status(int* status, void* stream) {
     unsigned int s = 0;
     cudaError_t e = pw::read_and_clear_status(&s, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "pw_device_status");
-    *status = (s & 1u) ? PW_ETIMEOUT : PW_OK;
+    *status = (s & 1u) ? PW_ETIMEOUT : (s & 2u) ? PW_EINVAL : PW_OK;
+    return PW_OK;
+}
+
+extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, const void* w, const pw_coeffs* c,
+                                 const pw_dims* dims, const void* gsu, const void* gsv, const void* gsw, void* gu,
+                                 void* gv, void* gw, int accumulate, void* stream) {
+    const char* who = "pw_advect_adjoint";
+    if (dtype != PW_F64 && dtype != PW_F32)
+        return fail(known_dtype(dtype) ? PW_EUNSUPPORTED : PW_EINVAL, "%s: dtype must be PW_F64 or PW_F32", who);
+    const int es = elem_size(dtype);
+    int rc = check_dims(dims, es, who);
+    if (rc) return rc;
+    if (!c) return fail(PW_ENULL, "%s: coeffs is NULL", who);
+    if (!c->tzc1 || !c->tzc2 || !c->tzd1 || !c->tzd2)
+        return fail(PW_ENULL, "%s: coefficient arrays are required", who);
+    const void* ptrs[9] = {u, v, w, gsu, gsv, gsw, gu, gv, gw};
+    const char* names[9] = {"u", "v", "w", "gsu", "gsv", "gsw", "gu", "gv", "gw"};
+    for (int n = 0; n < 9; ++n)
+        if ((rc = check_ptr(ptrs[n], es, names[n], who))) return rc;
+    for (int n = 1; n < 6; ++n)
+        if ((uintptr_t)ptrs[n] % 16 != (uintptr_t)u % 16)
+            return fail(PW_EINVAL, "%s: u, v, w, gsu, gsv, gsw must have the same address modulo 16 bytes", who);
+    const long long ext = field_extent_bytes(*dims, es);
+    for (int o = 6; o < 9; ++o) {
+        for (int n = 0; n < o; ++n)
+            if (overlap(ptrs[o], ext, ptrs[n], ext))
+                return fail(PW_EALIAS, "%s: output %s overlaps %s", who, names[o], names[n]);
+    }
+    const pw::TileShape shp = pw::adjoint_shape(es);
+    CUtensorMap maps[6];
+    for (int n = 0; n < 6; ++n)
+        if ((rc = make_field_map(&maps[n], ptrs[n], es, *dims, shp.box_x, shp.box_y))) return rc;
+    pw::AdjArgs a;
+    a.nx = dims->nx;
+    a.ny = dims->ny;
+    a.nz = dims->nz;
+    a.sy = dims->sy;
+    a.sz = dims->sz;
+    a.xoff = (int)(((uintptr_t)u % 16) / es);
+    a.tcx = c->tcx;
+    a.tcy = c->tcy;
+    a.tzc1 = c->tzc1;
+    a.tzc2 = c->tzc2;
+    a.tzd1 = c->tzd1;
+    a.tzd2 = c->tzd2;
+    a.gu = gu;
+    a.gv = gv;
+    a.gw = gw;
+    a.accumulate = accumulate ? 1 : 0;
+    cudaError_t e = pw::launch_adjoint(maps, es, a, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return PW_OK;
+}
+
+extern "C" int pw_fold_periodic_halo(pw_dtype dtype, void* field, const pw_dims* dims, void* stream) {
+    const char* who = "pw_fold_periodic_halo";
+    if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
+    const int es = elem_size(dtype);
+    int rc = check_dims(dims, es, who);
+    if (rc) return rc;
+    if (!field) return fail(PW_ENULL, "%s: field is NULL", who);
+    if (((uintptr_t)field) % es != 0) return fail(PW_EINVAL, "%s: field is misaligned", who);
+    cudaError_t e = pw::launch_fold_halo(field, es, dims->nx, dims->ny, dims->nz, dims->sy, dims->sz,
+                                         static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------- batches
+
+extern "C" size_t pw_batch_plan_bytes(int n) { return pw::batch_plan_bytes(n); }
+
+extern "C" int pw_variant_count(pw_dtype dtype) {
+    switch (dtype) {
+        case PW_F32:
+        case PW_F32_SPLIT: return pw::split_variant_count();
+        case PW_F64_PAIRED: return 1;
+        default: return 0;
+    }
+}
+
+extern "C" int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain* doms, int variant, void* plan_host,
+                                  size_t plan_bytes, long long* n_items) {
+    const char* who = "pw_make_batch_plan";
+    if (!doms || !plan_host || !n_items) return fail(PW_ENULL, "%s: doms, plan_host and n_items are required", who);
+    if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
+    if (dtype == PW_F64) return fail(PW_EUNSUPPORTED, "%s: PW_F64 has no batched kernel (use PW_F64_PAIRED)", who);
+    if (n < 1) return fail(PW_EINVAL, "%s: n must be >= 1", who);
+    if (variant < 0 || variant >= pw_variant_count(dtype))
+        return fail(PW_EINVAL, "%s: variant %d out of range for this dtype", who, variant);
+    if (plan_bytes < pw::batch_plan_bytes(n))
+        return fail(PW_EINVAL, "%s: plan_bytes %zu < %zu", who, plan_bytes, pw::batch_plan_bytes(n));
+    if (((uintptr_t)plan_host) % 64 != 0) return fail(PW_EINVAL, "%s: plan_host must be 64-byte aligned", who);
+    const int es = elem_size(dtype);
+    const pw::TileShape shp = dtype == PW_F64_PAIRED ? pw::fwd_paired_shape() : pw::fwd_split_shape_variant(variant);
+    // tallest domains first: their tiles take longest, so they start first
+    std::vector<int> order(n);
+    for (int d = 0; d < n; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return doms[a].dims.nz > doms[b].dims.nz; });
+    pw::BatchPlan* plan = static_cast<pw::BatchPlan*>(plan_host);
+    memset(plan_host, 0, pw::batch_plan_bytes(n));
+    long long items = 0;
+    for (int q = 0; q < n; ++q) {
+        const int d = order[q];
+        const pw_domain& dm = doms[d];
+        char tag[64];
+        snprintf(tag, sizeof(tag), "%s: domain %d", who, d);
+        int rc = check_dims(&dm.dims, es, tag);
+        if (rc) return rc;
+        const void* ptrs[6] = {dm.u, dm.v, dm.w, dm.su, dm.sv, dm.sw};
+        const char* names[6] = {"u", "v", "w", "su", "sv", "sw"};
+        for (int k = 0; k < 6; ++k)
+            if ((rc = check_ptr(ptrs[k], es, names[k], tag))) return rc;
+        if ((uintptr_t)dm.v % 16 != (uintptr_t)dm.u % 16 || (uintptr_t)dm.w % 16 != (uintptr_t)dm.u % 16)
+            return fail(PW_EINVAL, "%s: u, v and w must have the same address modulo 16 bytes", tag);
+        const bool f32 = (dtype == PW_F32 || dtype == PW_F32_SPLIT);
+        if (f32 && !dm.split) return fail(PW_ENULL, "%s: the split table is required", tag);
+        if (f32 && ((uintptr_t)dm.split) % 16 != 0) return fail(PW_EINVAL, "%s: split table not 16-byte aligned", tag);
+        if (!f32 && (!dm.coeffs.tzc1 || !dm.coeffs.tzc2 || !dm.coeffs.tzd1 || !dm.coeffs.tzd2))
+            return fail(PW_ENULL, "%s: coefficient arrays are required", tag);
+        const long long ext = field_extent_bytes(dm.dims, es);
+        for (int o = 3; o < 6; ++o)
+            for (int k = 0; k < o; ++k)
+                if (overlap(ptrs[o], ext, ptrs[k], ext))
+                    return fail(PW_EALIAS, "%s: output %s overlaps %s", tag, names[o], names[k]);
+        pw::BatchDomain& bd = plan->dom[q];
+        if ((rc = make_field_map(&bd.mu, dm.u, es, dm.dims, shp.box_x, shp.box_y))) return rc;
+        if ((rc = make_field_map(&bd.mv, dm.v, es, dm.dims, shp.box_x, shp.box_y))) return rc;
+        if ((rc = make_field_map(&bd.mw, dm.w, es, dm.dims, shp.box_x, shp.box_y))) return rc;
+        pw::FwdArgs& a = bd.args;
+        a.nx = dm.dims.nx;
+        a.ny = dm.dims.ny;
+        a.nz = dm.dims.nz;
+        a.sy = dm.dims.sy;
+        a.sz = dm.dims.sz;
+        a.xoff = (int)(((uintptr_t)dm.u % 16) / es);
+        a.vec = 1;
+        for (int k = 0; k < 6; ++k)
+            if (((uintptr_t)ptrs[k] + es) % 16 != 0) a.vec = 0;
+        a.tcx = dm.coeffs.tcx;
+        a.tcy = dm.coeffs.tcy;
+        a.tzc1 = dm.coeffs.tzc1;
+        a.tzc2 = dm.coeffs.tzc2;
+        a.tzd1 = dm.coeffs.tzd1;
+        a.tzd2 = dm.coeffs.tzd2;
+        a.split = static_cast<const float*>(dm.split);
+        a.su = dm.su;
+        a.sv = dm.sv;
+        a.sw = dm.sw;
+        bd.tiles_x = (dm.dims.nx + shp.tx - 1) / shp.tx;
+        bd.tiles_y = (dm.dims.ny + shp.ty - 1) / shp.ty;
+        bd.first_item = items;
+        items += (long long)bd.tiles_x * bd.tiles_y;
+    }
+    plan->counter = 0;
+    plan->n_items = items;
+    plan->n_domains = n;
+    plan->dtype = (int)dtype;
+    plan->variant = variant;
+    *n_items = items;
+    return PW_OK;
+}
+
+extern "C" int pw_advect_batched(pw_dtype dtype, int variant, void* plan_dev, long long n_items, void* stream) {
+    const char* who = "pw_advect_batched";
+    if (!plan_dev) return fail(PW_ENULL, "%s: plan_dev is NULL", who);
+    if (((uintptr_t)plan_dev) % 64 != 0) return fail(PW_EINVAL, "%s: plan_dev must be 64-byte aligned", who);
+    if (dtype != PW_F64_PAIRED && dtype != PW_F32 && dtype != PW_F32_SPLIT)
+        return fail(known_dtype(dtype) ? PW_EUNSUPPORTED : PW_EINVAL, "%s: no batched kernel for dtype %d", who,
+                    (int)dtype);
+    if (variant < 0 || variant >= pw_variant_count(dtype)) return fail(PW_EINVAL, "%s: bad variant", who);
+    if (n_items < 1) return fail(PW_EINVAL, "%s: n_items must be >= 1", who);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    pw::BatchPlan* plan = static_cast<pw::BatchPlan*>(plan_dev);
+    cudaError_t e = cudaMemsetAsync(&plan->counter, 0, sizeof(plan->counter), st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(plan, n_items, st)
+                               : pw::launch_split_batched(variant, plan, n_items, st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;
 }

@@ -14,8 +14,10 @@ namespace pw {
 // never lands, in which case the kernel records PW status and returns.
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;
 
-// Bit set in the device status word when a bounded wait expired.
+// Bits of the device status word: a bounded wait expired; a batched kernel
+// was given a plan built for another dtype or variant.
 constexpr unsigned int kStatusTimeout = 1u;
+constexpr unsigned int kStatusBadPlan = 2u;
 
 namespace {
 // Device status word of this translation unit (each kernel .cu file has its

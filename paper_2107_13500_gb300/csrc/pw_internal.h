@@ -5,11 +5,15 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 namespace pw {
 
 struct FwdArgs {
     int nx, ny, nz;
     long long sy, sz;          // element strides of every field
+    int xoff;                  // elements from the descriptors' 16-byte base to i = 0
+    int vec;                   // 1: every field's interior i = 1 starts on 16 bytes
     double tcx, tcy;
     const double *tzc1, *tzc2, *tzd1, *tzd2;
     const float* split;        // PW_F32_SPLIT table, else nullptr
@@ -28,12 +32,87 @@ TileShape fwd_f64_shape();
 TileShape fwd_paired_shape();
 TileShape fwd_split_shape();
 
+// ---------------------------------------------------------------- batches
+// One domain of a batch: its three TMA descriptors (in device memory, so the
+// persistent kernel can switch domains per work item), its launch arguments,
+// its tile grid and the index of its first work item.
+struct BatchDomain {
+    CUtensorMap mu, mv, mw;
+    FwdArgs args;
+    int tiles_x, tiles_y;
+    long long first_item;
+};
+
+// A batch plan as laid out in device memory: header, then n_domains entries.
+// `counter` is the persistent kernel's work queue (scratch: reset to 0 before
+// every launch).
+struct BatchPlan {
+    unsigned long long counter;
+    long long n_items;
+    int n_domains;
+    int dtype;
+    int variant;
+    int reserved;
+    BatchDomain dom[1];
+};
+
+inline size_t batch_plan_bytes(int n) {
+    return offsetof(BatchPlan, dom) + (size_t)(n > 0 ? n : 1) * sizeof(BatchDomain);
+}
+
+// Domain holding work item `item` (domains are stored in item order).
+__device__ __forceinline__ int find_domain(const BatchPlan* plan, long long item) {
+    int lo = 0, hi = plan->n_domains - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (plan->dom[mid].first_item <= item) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Grid of a persistent kernel: resident CTAs on every SM, at most n_items.
+template <typename Kern>
+cudaError_t persistent_grid(Kern kern, int threads, int smem, long long n_items, long long* grid) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
+    long long g = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    *grid = g < n_items ? g : n_items;
+    return cudaSuccess;
+}
+
+int split_variant_count();
+TileShape fwd_split_shape_variant(int v);
+cudaError_t launch_fwd_split_variant(int v, const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
+                                     const FwdArgs& a, cudaStream_t st);
+cudaError_t launch_split_batched(int v, BatchPlan* plan, long long n_items, cudaStream_t st);
+cudaError_t launch_paired_batched(BatchPlan* plan, long long n_items, cudaStream_t st);
+
 cudaError_t launch_fwd_f64(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                            const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_fwd_paired(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                               const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_fwd_split(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                              const FwdArgs& a, cudaStream_t st);
+
+struct AdjArgs {
+    int nx, ny, nz;
+    long long sy, sz;
+    int xoff;                  // elements from the descriptors' 16-byte base to i = 0
+    double tcx, tcy;
+    const double *tzc1, *tzc2, *tzd1, *tzd2;
+    void *gu, *gv, *gw;
+    int accumulate;
+};
+
+TileShape adjoint_shape(int elem_bytes);
+// maps6: u, v, w, gsu, gsv, gsw
+cudaError_t launch_adjoint(const CUtensorMap* maps6, int elem_bytes, const AdjArgs& a, cudaStream_t st);
+cudaError_t launch_fold_halo(void* field, int elem_bytes, int nx, int ny, int nz, long long sy, long long sz,
+                             cudaStream_t st);
 
 cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz, long long sy, long long sz,
                              cudaStream_t st);
@@ -45,5 +124,6 @@ cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, fl
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_paired(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_split(unsigned int* status, cudaStream_t st);
+cudaError_t read_and_clear_status_adjoint(unsigned int* status, cudaStream_t st);
 
 }  // namespace pw

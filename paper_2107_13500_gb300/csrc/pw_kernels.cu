@@ -48,10 +48,10 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
     __syncthreads();
     int issued = 0;  // meaningful in thread 0 only
     if (tid == 0) {
-        for (; issued < S && issued < nz; ++issued) ring.issue(issued, &mu, &mv, &mw, x0, y0);
+        for (; issued < S && issued < nz; ++issued) ring.issue(issued, issued, &mu, &mv, &mw, x0, y0);
     }
 
-    const int c0 = (ty + 1) * BX + (tx + 1);
+    const int c0 = (ty + 1) * BX + (tx + 1) + a.xoff;
     double* __restrict__ su = static_cast<double*>(a.su);
     double* __restrict__ sv = static_cast<double*>(a.sv);
     double* __restrict__ sw = static_cast<double*>(a.sw);
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
     bool abort = __syncthreads_or(bad);
     if (!abort && tid == 0 && issued < nz) {
         fence_proxy_async_smem();
-        ring.issue(issued, &mu, &mv, &mw, x0, y0);
+        ring.issue(issued, issued, &mu, &mv, &mw, x0, y0);
         ++issued;
     }
 
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
         abort = __syncthreads_or(bad);  // also releases level k's stage
         if (!abort && tid == 0 && issued < nz) {
             fence_proxy_async_smem();
-            ring.issue(issued, &mu, &mv, &mw, x0, y0);
+            ring.issue(issued, issued, &mu, &mv, &mw, x0, y0);
             ++issued;
         }
     }
@@ -242,11 +242,12 @@ cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, fl
 // ---------------------------------------------------------------------------
 
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st) {
-    unsigned int parts[3] = {0, 0, 0};
+    unsigned int parts[4] = {0, 0, 0, 0};
     cudaError_t e = read_and_clear_tu_status(&parts[0], st);
     if (e == cudaSuccess) e = read_and_clear_status_paired(&parts[1], st);
     if (e == cudaSuccess) e = read_and_clear_status_split(&parts[2], st);
-    *status = parts[0] | parts[1] | parts[2];
+    if (e == cudaSuccess) e = read_and_clear_status_adjoint(&parts[3], st);
+    *status = parts[0] | parts[1] | parts[2] | parts[3];
     return e;
 }
 

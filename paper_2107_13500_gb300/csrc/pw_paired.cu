@@ -8,9 +8,12 @@
 // Step k computes level k from the pairs of levels k and k+1 plus pairs of
 // level k-1 carried in registers (own-column values and face sums of w).
 // Per level: wait(k+1) -> split(k+1) -> barrier -> compute(k) -> barrier.
+// Loads are numbered per CTA (`seq`), so the persistent form can run many
+// tiles of many domains through one ring (see pw_ring.cuh).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "pw.h"
 #include "pw_common.cuh"
 #include "pw_internal.h"
 #include "pw_pair.cuh"
@@ -26,15 +29,17 @@ constexpr int kBoxElems = Shape::BX * Shape::BY;
 // pair buffers: [2 levels][3 fields][box] float2, then [2 levels][4] coefficient pairs
 constexpr int kPairBytes = 2 * 3 * kBoxElems * 8;
 constexpr int kCoefBytes = 2 * 4 * 8;
-// ring stages | ring barriers (S x 8 B, padded to 64 B) | pairs | coefficient pairs,
-// plus 128 B of slack for aligning the ring base
+// ring stages | ring barriers (S x 8 B, padded to 64 B) | pairs | coefficient
+// pairs | work-item slot, plus 128 B of slack for aligning the ring base
 constexpr int kPairOffset = Shape::S * Shape::STAGE_BYTES + 64;
-constexpr int kSmemBytes = kPairOffset + kPairBytes + kCoefBytes + 128;
+constexpr int kItemOffset = kPairOffset + kPairBytes + kCoefBytes;
+constexpr int kSmemBytes = kItemOffset + 16 + 128;
 static_assert(Shape::S * 8 <= 64, "ring barriers must fit before the pair buffers");
 
 struct PairSmem {
-    float2* pairs;  // [2][3][kBoxElems]
-    float2* coef;   // [2][4]: tzc1, tzc2, tzd1, tzd2 of a level
+    float2* pairs;    // [2][3][kBoxElems]
+    float2* coef;     // [2][4]: tzc1, tzc2, tzd1, tzd2 of a level
+    long long* item;  // work item handed from thread 0 to the CTA
     __device__ __forceinline__ const pf* field(int lev, int f) const {
         return reinterpret_cast<const pf*>(pairs + ((lev & 1) * 3 + f) * kBoxElems);
     }
@@ -44,13 +49,13 @@ struct PairSmem {
     }
 };
 
-// Split level `lev` (its TMA stage) into pairs; threads 0..3 also split the
+// Split load `seq` (= level `lev`) into pairs; threads 0..3 also split the
 // level's four vertical coefficients.
-__device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, int lev, const FwdArgs& a,
-                                              int tid) {
+__device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, long long seq, int lev,
+                                              const FwdArgs& a, int tid) {
     float2* dst = ps.pairs + (lev & 1) * 3 * kBoxElems;
     for (int f = 0; f < 3; ++f) {
-        const double* src = ring.template box<double>(lev, f);
+        const double* src = ring.template box<double>(seq, f);
         for (int e = tid; e < kBoxElems; e += Shape::NT) {
             const pf p = split_double(src[e]);
             dst[f * kBoxElems + e] = make_float2(p.h, p.l);
@@ -68,39 +73,26 @@ __device__ __forceinline__ pf ld(const pf* b, int idx) {
     return {v.x, v.y};
 }
 
-__global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
-                                                               const __grid_constant__ CUtensorMap mv,
-                                                               const __grid_constant__ CUtensorMap mw,
-                                                               const FwdArgs a) {
+// One tile (bx, by) of domain `a`; `seq` is the CTA's running load count.
+// Returns false if a bounded wait expired (status set, copies drained).
+__device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtensorMap* mu, const CUtensorMap* mv,
+                            const CUtensorMap* mw, const FwdArgs& a, int bx, int by, long long& seq, int tid) {
     constexpr int TX = Shape::TX, S = Shape::S, BX = Shape::BX;
-    extern __shared__ unsigned char smem_raw[];
-    Ring<Shape> ring;
-    ring.setup(smem_raw);
-    PairSmem ps;
-    ps.pairs = reinterpret_cast<float2*>(ring.base + kPairOffset);
-    ps.coef = ps.pairs + 2 * 3 * kBoxElems;
-
-    const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * Shape::TY;
+    const int x0 = bx * TX, y0 = by * Shape::TY;
     const int i = x0 + 1 + tx, j = y0 + 1 + ty;
     const bool act = (i <= a.nx) && (j <= a.ny);
     const int nz = a.nz;
+    const long long s0 = seq;
 
-    if (tid == 0) {
-        prefetch_tensormap(&mu);
-        prefetch_tensormap(&mv);
-        prefetch_tensormap(&mw);
-        ring.init_barriers();
-    }
-    __syncthreads();
     int issued = 0;
     if (tid == 0) {
-        for (; issued < S && issued < nz; ++issued) ring.issue(issued, &mu, &mv, &mw, x0, y0);
+        fence_proxy_async_smem();
+        for (; issued < S && issued < nz; ++issued) ring.issue(s0 + issued, issued, mu, mv, mw, x0, y0);
     }
 
     const pf tcx = split_double(a.tcx), tcy = split_double(a.tcy);
-    const int c0 = (ty + 1) * BX + (tx + 1);
+    const int c0 = (ty + 1) * BX + (tx + 1) + a.xoff;
     double* __restrict__ su = static_cast<double*>(a.su);
     double* __restrict__ sv = static_cast<double*>(a.sv);
     double* __restrict__ sw = static_cast<double*>(a.sw);
@@ -111,13 +103,13 @@ __global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_cons
     const int pre = nz > 1 ? 2 : 1;
     bool bad = false;
     for (int lev = 0; lev < pre; ++lev) {
-        bad |= !ring.wait(lev);
-        convert_level(ring, ps, lev, a, tid);
+        bad |= !ring.wait(s0 + lev);
+        convert_level(ring, ps, s0 + lev, lev, a, tid);
     }
     bool abort = __syncthreads_or(bad);
     if (!abort && tid == 0) {
         fence_proxy_async_smem();
-        for (int n = 0; n < pre && issued < nz; ++n, ++issued) ring.issue(issued, &mu, &mv, &mw, x0, y0);
+        for (int n = 0; n < pre && issued < nz; ++n, ++issued) ring.issue(s0 + issued, issued, mu, mv, mw, x0, y0);
     }
 
     pf uo_m, vo_m, wo_m, wx_m, wy_m, wz_m;
@@ -144,13 +136,13 @@ __global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_cons
         const bool top = (k == nz - 1);
         if (!top) {
             // split level k+1 (its pair slot held level k-1, consumed last step)
-            bad |= !ring.wait(k + 1);
-            convert_level(ring, ps, k + 1, a, tid);
+            bad |= !ring.wait(s0 + k + 1);
+            convert_level(ring, ps, s0 + k + 1, k + 1, a, tid);
             abort = __syncthreads_or(bad);
             if (abort) break;
             if (tid == 0 && issued < nz) {
                 fence_proxy_async_smem();
-                ring.issue(issued, &mu, &mv, &mw, x0, y0);
+                ring.issue(s0 + issued, issued, mu, mv, mw, x0, y0);
                 ++issued;
             }
         }
@@ -204,9 +196,71 @@ __global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_cons
         wz_m = wz;
         abort = __syncthreads_or(bad);  // level k's pairs are free after this
     }
-    if (abort && tid == 0) {
-        atomicOr(&tu_status, kStatusTimeout);
-        for (int lev = (issued > S ? issued - S : 0); lev < issued; ++lev) (void)ring.wait(lev);
+    if (abort) {
+        if (tid == 0) {
+            atomicOr(&tu_status, kStatusTimeout);
+            for (int lev = (issued > S ? issued - S : 0); lev < issued; ++lev) (void)ring.wait(s0 + lev);
+        }
+        return false;
+    }
+    seq = s0 + nz;
+    return true;
+}
+
+__device__ __forceinline__ void setup_smem(unsigned char* raw, Ring<Shape>& ring, PairSmem& ps) {
+    ring.setup(raw);
+    ps.pairs = reinterpret_cast<float2*>(ring.base + kPairOffset);
+    ps.coef = ps.pairs + 2 * 3 * kBoxElems;
+    ps.item = reinterpret_cast<long long*>(ring.base + kItemOffset);
+}
+
+__global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
+                                                               const __grid_constant__ CUtensorMap mv,
+                                                               const __grid_constant__ CUtensorMap mw,
+                                                               const FwdArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    Ring<Shape> ring;
+    PairSmem ps;
+    setup_smem(smem_raw, ring, ps);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        prefetch_tensormap(&mu);
+        prefetch_tensormap(&mv);
+        prefetch_tensormap(&mw);
+        ring.init_barriers();
+    }
+    __syncthreads();
+    long long seq = 0;
+    (void)paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, seq, tid);
+}
+
+// Persistent form over a batch plan: work items (one tile of one domain)
+// come from the plan's counter, at most n_items iterations.
+__global__ void __launch_bounds__(Shape::NT) fwd_paired_batched(BatchPlan* plan) {
+    extern __shared__ unsigned char smem_raw[];
+    Ring<Shape> ring;
+    PairSmem ps;
+    setup_smem(smem_raw, ring, ps);
+    const int tid = threadIdx.x;
+    if (plan->variant != 0 || plan->dtype != PW_F64_PAIRED) {
+        if (tid == 0) atomicOr(&tu_status, kStatusBadPlan);
+        return;
+    }
+    if (tid == 0) ring.init_barriers();
+    __syncthreads();
+    const long long n_items = plan->n_items;
+    long long seq = 0;
+    for (long long it = 0; it < n_items; ++it) {
+        if (tid == 0) *ps.item = (long long)atomicAdd(&plan->counter, 1ull);
+        __syncthreads();
+        const long long item = *ps.item;
+        __syncthreads();  // every thread has read the slot before thread 0 rewrites it
+        if (item >= n_items) break;
+        const BatchDomain& d = plan->dom[find_domain(plan, item)];
+        const long long t = item - d.first_item;
+        if (!paired_tile(ring, ps, &d.mu, &d.mv, &d.mw, d.args, (int)(t % d.tiles_x), (int)(t / d.tiles_x), seq,
+                         tid))
+            break;
     }
 }
 
@@ -224,6 +278,17 @@ cudaError_t launch_fwd_paired(const CUtensorMap& mu, const CUtensorMap& mv, cons
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY);
     fwd_paired_kernel<<<grid, Shape::NT, kSmemBytes, st>>>(mu, mv, mw, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_paired_batched(BatchPlan* plan, long long n_items, cudaStream_t st) {
+    cudaError_t e =
+        cudaFuncSetAttribute(fwd_paired_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    long long grid = 0;
+    if ((e = persistent_grid(fwd_paired_batched, Shape::NT, kSmemBytes, n_items, &grid)) != cudaSuccess) return e;
+    if (grid < 1) return cudaSuccess;
+    fwd_paired_batched<<<(unsigned)grid, Shape::NT, kSmemBytes, st>>>(plan);
     return cudaGetLastError();
 }
 

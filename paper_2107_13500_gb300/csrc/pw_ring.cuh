@@ -20,8 +20,12 @@ template <typename T, int TX_, int TY_, int S_>
 struct RingShape {
     static constexpr int TX = TX_, TY = TY_, S = S_;
     static constexpr int NT = TX * TY;
-    // box inner extent must be a whole number of 16-byte units
-    static constexpr int BX = round_up(TX + 2, 16 / (int)sizeof(T));
+    // Element offset of the halo column i = 0 from the 16-byte boundary the
+    // TMA descriptor starts at: 0 .. XOFF_MAX (the caller's base pointer
+    // need only be element-aligned). The box covers the tile, its halo and
+    // that offset, and its inner extent is a whole number of 16-byte units.
+    static constexpr int XOFF_MAX = 16 / (int)sizeof(T) - 1;
+    static constexpr int BX = round_up(TX + 2 + XOFF_MAX, 16 / (int)sizeof(T));
     static constexpr int BY = TY + 2;
     static constexpr int BOX_BYTES = BX * BY * (int)sizeof(T);
     static constexpr int BOX_STRIDE = round_up(BOX_BYTES, 128);
@@ -31,31 +35,35 @@ struct RingShape {
     static_assert((TX * (int)sizeof(T)) % 16 == 0, "tile x origin must stay 16-byte aligned");
 };
 
-// Shared-memory ring. Level `lev` lives in stage lev % S; its barrier phase
-// is lev / S, so the parity to wait for is (lev / S) & 1.
+// Shared-memory ring addressed by load number: the CTA numbers its level
+// loads 0, 1, 2, ... across every tile it processes; load `seq` lives in
+// stage seq % S and completes barrier phase seq / S, so the parity to wait
+// for is (seq / S) & 1. A one-shot kernel simply starts at seq = 0.
 template <typename Shape>
 struct Ring {
     unsigned char* base;  // 128-byte aligned
     uint64_t* full;       // S barriers
 
+    // `raw` must be the kernel's extern __shared__ array: the base is found by
+    // pointer arithmetic on it (not through an integer), so the compiler keeps
+    // every derived access in the shared address space (LDS, not generic LD).
     __device__ __forceinline__ void setup(unsigned char* raw) {
-        uintptr_t p = reinterpret_cast<uintptr_t>(raw);
-        p = (p + 127) & ~uintptr_t(127);
-        base = reinterpret_cast<unsigned char*>(p);
+        base = raw + ((128u - (smem_addr(raw) & 127u)) & 127u);
         full = reinterpret_cast<uint64_t*>(base + Shape::S * Shape::STAGE_BYTES);
     }
     template <typename T>
-    __device__ __forceinline__ const T* box(int lev, int field) const {
-        return reinterpret_cast<const T*>(base + (lev % Shape::S) * Shape::STAGE_BYTES + field * Shape::BOX_STRIDE);
+    __device__ __forceinline__ const T* box(long long seq, int field) const {
+        return reinterpret_cast<const T*>(base + (int)(seq % Shape::S) * Shape::STAGE_BYTES +
+                                          field * Shape::BOX_STRIDE);
     }
     __device__ __forceinline__ void init_barriers() {
         for (int s = 0; s < Shape::S; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
-    // Issue the three box loads of level `lev` (called by one thread).
-    __device__ __forceinline__ void issue(int lev, const CUtensorMap* mu, const CUtensorMap* mv,
+    // Issue the three box loads of level `lev` as load number `seq` (one thread).
+    __device__ __forceinline__ void issue(long long seq, int lev, const CUtensorMap* mu, const CUtensorMap* mv,
                                           const CUtensorMap* mw, int x0, int y0) {
-        const int s = lev % Shape::S;
+        const int s = (int)(seq % Shape::S);
         uint64_t* bar = &full[s];
         unsigned char* dst = base + s * Shape::STAGE_BYTES;
         mbar_arrive_expect_tx(bar, 3 * Shape::BOX_BYTES);
@@ -63,8 +71,8 @@ struct Ring {
         tma_load_3d(dst + Shape::BOX_STRIDE, mv, bar, x0, y0, lev);
         tma_load_3d(dst + 2 * Shape::BOX_STRIDE, mw, bar, x0, y0, lev);
     }
-    __device__ __forceinline__ bool wait(int lev) {
-        return mbar_wait_bounded(&full[lev % Shape::S], (uint32_t)((lev / Shape::S) & 1));
+    __device__ __forceinline__ bool wait(long long seq) {
+        return mbar_wait_bounded(&full[(int)(seq % Shape::S)], (uint32_t)((seq / Shape::S) & 1));
     }
 };
 

@@ -29,12 +29,13 @@ PW_ETIMEOUT = -6
 PW_F64 = 0
 PW_F32_SPLIT = 1
 PW_F64_PAIRED = 2
+PW_F32 = 3
 PW_SPLIT_NCOEF = 32
 
-MODES = {"f64": PW_F64, "paired": PW_F64_PAIRED, "split": PW_F32_SPLIT}
+MODES = {"f64": PW_F64, "paired": PW_F64_PAIRED, "split": PW_F32_SPLIT, "f32": PW_F32}
 
 # Algorithmic HBM traffic per point: read u, v, w once, write su, sv, sw once.
-BYTES_PER_POINT = {"f64": 48, "paired": 48, "split": 24}
+BYTES_PER_POINT = {"f64": 48, "paired": 48, "split": 24, "f32": 24}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpw.so")
@@ -56,6 +57,12 @@ class Coeffs(ctypes.Structure):
     _fields_ = [("tcx", ctypes.c_double), ("tcy", ctypes.c_double),
                 ("tzc1", ctypes.c_void_p), ("tzc2", ctypes.c_void_p),
                 ("tzd1", ctypes.c_void_p), ("tzd2", ctypes.c_void_p)]
+
+
+class Domain(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("su", ctypes.c_void_p), ("sv", ctypes.c_void_p), ("sw", ctypes.c_void_p),
+                ("dims", Dims), ("coeffs", Coeffs), ("split", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -89,10 +96,20 @@ def load_library(path: str | None = None):
         for name in ("pw_make_coeffs", "pw_fill_periodic_halo", "pw_advect", "pw_make_split_table",
                      "pw_split_field", "pw_device_status"):
             getattr(lib, name).restype = ctypes.c_int
-        if hasattr(lib, "pw_advect_adjoint"):
-            lib.pw_advect_adjoint.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(Coeffs),
-                                              ctypes.POINTER(Dims), vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
-            lib.pw_advect_adjoint.restype = ctypes.c_int
+        lib.pw_advect_adjoint.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.POINTER(Coeffs),
+                                          ctypes.POINTER(Dims), vp, vp, vp, vp, vp, vp, ctypes.c_int, vp]
+        lib.pw_advect_adjoint.restype = ctypes.c_int
+        lib.pw_fold_periodic_halo.argtypes = [ctypes.c_int, vp, ctypes.POINTER(Dims), vp]
+        lib.pw_fold_periodic_halo.restype = ctypes.c_int
+        lib.pw_batch_plan_bytes.argtypes = [ctypes.c_int]
+        lib.pw_batch_plan_bytes.restype = ctypes.c_size_t
+        lib.pw_variant_count.argtypes = [ctypes.c_int]
+        lib.pw_variant_count.restype = ctypes.c_int
+        lib.pw_make_batch_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(Domain), ctypes.c_int, vp,
+                                           ctypes.c_size_t, ctypes.POINTER(ctypes.c_longlong)]
+        lib.pw_make_batch_plan.restype = ctypes.c_int
+        lib.pw_advect_batched.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong, vp]
+        lib.pw_advect_batched.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -113,11 +130,47 @@ def row_stride(nx: int, elem_bytes: int) -> int:
     return ((nx + 2 + per - 1) // per) * per
 
 
-def empty_field(nx, ny, nz, dtype=None, device="cuda"):
+def _aligned_zeros(shape, dtype, device, lead):
+    """Zeros of `shape` (C order) whose first element sits `lead` elements
+    past a 16-byte boundary (torch's allocator returns 512-byte blocks)."""
+    import torch
+    n = 1
+    for d in shape:
+        n *= d
+    flat = torch.zeros(n + lead, dtype=dtype, device=device)
+    return flat[lead:].view(shape)
+
+
+def interior_lead(elem_bytes: int) -> int:
+    """Elements between a 16-byte boundary and the halo cell i = 0 that put
+    the first interior cell (i = 1) on the boundary: 1 double, 3 floats."""
+    return 16 // elem_bytes - 1
+
+
+def empty_field(nx, ny, nz, dtype=None, device="cuda", aligned=True):
+    """Zeroed field in the library's layout. aligned=True places i = 1 of
+    every row on a 16-byte boundary, which selects the vectorised kernels."""
     import torch
     dtype = dtype or torch.float64
     es = torch.empty((), dtype=dtype).element_size()
-    return torch.zeros((nz, ny + 2, row_stride(nx, es)), dtype=dtype, device=device)
+    shape = (nz, ny + 2, row_stride(nx, es))
+    return _aligned_zeros(shape, dtype, device, interior_lead(es) if aligned else 0)
+
+
+def field_like(t):
+    """Zeroed tensor with t's shape, dtype, device and 16-byte phase."""
+    es = t.element_size()
+    return _aligned_zeros(tuple(t.shape), t.dtype, t.device, (t.data_ptr() % 16) // es)
+
+
+def field_from_numpy(a, nx, dtype=None, device="cuda", aligned=True):
+    """Copy a numpy field [nz][ny+2][>= nx+2] into a new device field."""
+    import torch
+    dtype = dtype or torch.float64
+    t = empty_field(nx, a.shape[1] - 2, a.shape[0], dtype, device, aligned)
+    src = torch.from_numpy(np.ascontiguousarray(a[:, :, : nx + 2]))
+    t[:, :, : nx + 2].copy_(src.to(dtype))
+    return t
 
 
 def dims_of(t, nx: int, ny: int) -> Dims:
@@ -145,6 +198,15 @@ class Coefficients:
     tcy: float
     tz4: np.ndarray          # (4, nz): tzc1, tzc2, tzd1, tzd2
     dev: object = None        # torch (4, nz) float64 on the GPU
+    f32_table: object = None  # device table for PW_F32 (all means 0)
+
+    def zero_mean_table(self, device="cuda"):
+        """Device table for PW_F32: the split table with every mean 0."""
+        import torch
+        if self.f32_table is None or str(self.f32_table.device) != str(torch.device(device)):
+            z = np.zeros(self.nz)
+            self.f32_table = torch.from_numpy(make_split_table(self, z, z, z)).to(device)
+        return self.f32_table
 
     def to_device(self, device="cuda"):
         import torch
@@ -205,18 +267,19 @@ def advect(u, v, w, coeffs: Coefficients, nx, ny, mode="paired", split_table=Non
     """Source terms (su, sv, sw) of u, v, w.
 
     mode: "f64" (native FP64), "paired" (FP64 in/out, paired-FP32
-    arithmetic) or "split" (float perturbations; ``split_table`` is the
-    device table from :func:`make_split_table`).
+    arithmetic), "split" (float perturbations; ``split_table`` is the
+    device table from :func:`make_split_table`) or "f32" (float full fields).
     """
-    import torch
     lib = load_library()
     dt = MODES[mode]
+    if mode == "f32" and split_table is None:
+        split_table = coeffs.zero_mean_table(u.device)
     d = dims_of(u, nx, ny)
     for t in (v, w):
         if t.shape != u.shape or t.stride() != u.stride() or t.dtype != u.dtype:
             raise ValueError("u, v, w must share shape, strides and dtype")
     if out is None:
-        out = tuple(torch.empty_strided(u.shape, u.stride(), dtype=u.dtype, device=u.device) for _ in range(3))
+        out = tuple(field_like(u) for _ in range(3))
     su, sv, sw = out
     for t in out:
         if t.shape != u.shape or t.stride() != u.stride() or t.dtype != u.dtype:
@@ -247,3 +310,93 @@ def device_status(stream=None) -> int:
     st = ctypes.c_int(0)
     _check(load_library().pw_device_status(ctypes.byref(st), _stream_handle(stream)))
     return st.value
+
+
+def advect_adjoint(u, v, w, coeffs: Coefficients, nx, ny, gsu, gsv, gsw, mode="f64", out=None, accumulate=False,
+                   stream=None):
+    """(gu, gv, gw) = J(u, v, w)^T (gsu, gsv, gsw) on every cell the forward
+    reads (halo included). mode "f64" (double) or "f32" (float). Cotangents
+    must share u's layout (shape, strides, 16-byte phase)."""
+    lib = load_library()
+    dt = {"f64": PW_F64, "f32": PW_F32}[mode]
+    d = dims_of(u, nx, ny)
+    ins = (u, v, w, gsu, gsv, gsw)
+    for t in ins[1:]:
+        if t.shape != u.shape or t.stride() != u.stride() or t.dtype != u.dtype:
+            raise ValueError("u, v, w and the cotangents must share shape, strides and dtype")
+    if out is None:
+        out = tuple(field_like(u) for _ in range(3))
+    gu, gv, gw = out
+    c = coeffs.c_struct()
+    vp = ctypes.c_void_p
+    _check(lib.pw_advect_adjoint(dt, *(vp(t.data_ptr()) for t in ins[:3]), ctypes.byref(c), ctypes.byref(d),
+                                 *(vp(t.data_ptr()) for t in ins[3:]), vp(gu.data_ptr()), vp(gv.data_ptr()),
+                                 vp(gw.data_ptr()), 1 if accumulate else 0, _stream_handle(stream)))
+    return gu, gv, gw
+
+
+def fold_periodic_halo(g, nx, ny, stream=None):
+    """Transpose of fill_periodic_halo, in place: halo gradients are added to
+    the interior cells they were copied from, and the halo is zeroed."""
+    import torch
+    dt = PW_F32 if g.dtype == torch.float32 else PW_F64
+    d = dims_of(g, nx, ny)
+    _check(load_library().pw_fold_periodic_halo(dt, ctypes.c_void_p(g.data_ptr()), ctypes.byref(d),
+                                                _stream_handle(stream)))
+    return g
+
+
+# ---------------------------------------------------------------- batches
+
+def variant_count(mode) -> int:
+    return int(load_library().pw_variant_count(MODES[mode]))
+
+
+class Batch:
+    """Many independent domains evaluated by one persistent launch.
+
+    domains: sequence of dicts with keys u, v, w (inputs), su, sv, sw
+    (outputs; allocated with field_like(u) if absent), nx, ny, coeffs
+    (Coefficients) and, for "split", split_table. mode "paired", "f32" or
+    "split". The plan (TMA descriptors, work table and work-queue counter) is
+    built on the host and copied once into a device buffer owned here.
+    """
+
+    def __init__(self, domains, mode="paired", variant=0):
+        import torch
+        lib = load_library()
+        self.mode, self.variant = mode, int(variant)
+        self.dt = MODES[mode]
+        self.domains = []
+        cs = (Domain * len(domains))()
+        for n, d in enumerate(domains):
+            u = d["u"]
+            outs = tuple(d.get(k) if d.get(k) is not None else field_like(u) for k in ("su", "sv", "sw"))
+            dd = dict(d, su=outs[0], sv=outs[1], sw=outs[2])
+            split = d.get("split_table")
+            if mode == "f32" and split is None:
+                split = d["coeffs"].zero_mean_table(u.device)
+                dd["split_table"] = split
+            self.domains.append(dd)
+            cstruct = d["coeffs"].c_struct()
+            cs[n] = Domain(u.data_ptr(), d["v"].data_ptr(), d["w"].data_ptr(), outs[0].data_ptr(),
+                           outs[1].data_ptr(), outs[2].data_ptr(), dims_of(u, d["nx"], d["ny"]), cstruct,
+                           split.data_ptr() if split is not None else None)
+        nbytes = int(lib.pw_batch_plan_bytes(len(domains)))
+        raw = np.zeros(nbytes + 64, dtype=np.uint8)
+        off = (-raw.ctypes.data) % 64
+        host = raw[off:off + nbytes]
+        n_items = ctypes.c_longlong(0)
+        _check(lib.pw_make_batch_plan(self.dt, len(domains), cs, self.variant, ctypes.c_void_p(host.ctypes.data),
+                                      nbytes, ctypes.byref(n_items)))
+        self.n_items = int(n_items.value)
+        self.plan_host = host
+        self.plan_dev = torch.from_numpy(host.copy()).to(domains[0]["u"].device)
+        self.points = sum(d["u"].shape[0] * d["nx"] * d["ny"] for d in domains)
+
+    def run(self, stream=None):
+        _check(load_library().pw_advect_batched(self.dt, self.variant, ctypes.c_void_p(self.plan_dev.data_ptr()),
+                                                self.n_items, _stream_handle(stream)))
+
+    def outputs(self):
+        return [(d["su"], d["sv"], d["sw"]) for d in self.domains]

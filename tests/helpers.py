@@ -41,12 +41,9 @@ def to_numpy_f64(t, sy_np, nx):
     return out
 
 
-def to_device(a, nx, torch_dtype, device="cuda"):
-    """Numpy field -> GPU tensor in the library's padded layout for torch_dtype."""
-    import torch
+def to_device(a, nx, torch_dtype, device="cuda", aligned=True):
+    """Numpy field -> GPU tensor in the library's padded layout for torch_dtype.
+    aligned=True puts i = 1 on a 16-byte boundary (vectorised kernels);
+    aligned=False leaves i = 0 there (the kernels' general path)."""
     from paper_2107_13500_gb300 import pw
-    es = torch.empty((), dtype=torch_dtype).element_size()
-    sy = pw.row_stride(nx, es)
-    t = np.zeros((a.shape[0], a.shape[1], sy), dtype=np.float64)
-    t[:, :, : nx + 2] = a[:, :, : nx + 2]
-    return torch.from_numpy(t).to(device=device, dtype=torch_dtype)
+    return pw.field_from_numpy(a, nx, torch_dtype, device, aligned)

@@ -177,3 +177,46 @@ def test_split_table_algebra(lib, oracle_lib):
     for got, want in zip((su, sv, sw), ref):
         gi, wi = got[1:, 1:ny + 1, 1:nx + 1], want[1:, 1:ny + 1, 1:nx + 1]
         assert np.max(np.abs(gi - wi)) <= 1e-5 * np.max(np.abs(wi))
+
+
+def test_batch_plan_validation_without_device(lib):
+    """pw_make_batch_plan rejects bad requests before encoding anything."""
+    import ctypes
+    from paper_2107_13500_gb300 import pw
+    assert lib.pw_batch_plan_bytes(96) > lib.pw_batch_plan_bytes(1) > 0
+    assert lib.pw_variant_count(pw.PW_F32) == 5 and lib.pw_variant_count(pw.PW_F64_PAIRED) == 1
+    assert lib.pw_variant_count(pw.PW_F64) == 0
+    nbytes = lib.pw_batch_plan_bytes(2)
+    raw = np.zeros(nbytes + 128, dtype=np.uint8)
+    off = (-raw.ctypes.data) % 64
+    plan = ctypes.c_void_p(raw.ctypes.data + off)
+    doms = (pw.Domain * 2)()
+    n = ctypes.c_longlong(0)
+    assert lib.pw_make_batch_plan(pw.PW_F64, 2, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EUNSUPPORTED
+    assert lib.pw_make_batch_plan(pw.PW_F32, 0, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
+    assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 7, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
+    assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 0, plan, nbytes - 1, ctypes.byref(n)) == pw.PW_EINVAL
+    mis = ctypes.c_void_p(raw.ctypes.data + off + 8)
+    assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 0, mis, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
+    # zeroed domains: dims fail validation, naming the domain
+    assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
+    assert b"domain" in lib.pw_last_error()
+    assert lib.pw_advect_batched(pw.PW_F32, 0, None, 1, None) == pw.PW_ENULL
+    assert lib.pw_advect_batched(pw.PW_F64, 0, plan, 1, None) == pw.PW_EUNSUPPORTED
+
+
+def test_adjoint_validation_without_device(lib):
+    import ctypes
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 12, 6, 4
+    sy = pw.row_stride(nx, 8)
+    d = pw.Dims(nx, ny, nz, 1, sy, sy * (ny + 2))
+    c = pw.Coeffs(0.005, 0.005, 0x1000, 0x2000, 0x3000, 0x4000)
+    ext = nz * sy * (ny + 2) * 8
+    p = [ctypes.c_void_p((1 << 40) + k * ext) for k in range(9)]
+    assert lib.pw_advect_adjoint(pw.PW_F64_PAIRED, *p[:3], ctypes.byref(c), ctypes.byref(d), *p[3:], 0,
+                                 None) == pw.PW_EUNSUPPORTED
+    alias = p[:6] + [p[0]] + p[7:]
+    assert lib.pw_advect_adjoint(pw.PW_F64, *alias[:3], ctypes.byref(c), ctypes.byref(d), *alias[3:], 0,
+                                 None) == pw.PW_EALIAS
+    assert lib.pw_fold_periodic_halo(pw.PW_F64, None, ctypes.byref(d), None) == pw.PW_ENULL

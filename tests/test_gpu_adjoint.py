@@ -1,0 +1,192 @@
+"""GPU checks of the adjoint (pw_advect_adjoint), the halo fold and the
+autograd/rollout layer: against the oracle's scatter-form adjoint, the
+dot-product test <J d, y> = <d, J^T y> (1e-12 in FP64), finite differences
+of a checkpointed 20-step forward-Euler rollout, and exact transposition of
+the periodic halo fill.
+"""
+import numpy as np
+import pytest
+
+from helpers import to_device
+from paper_2107_13500_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2107_13500_gb300 import build, pw
+    build.build()
+    pw.load_library()
+    return torch
+
+
+def _raw(nx, ny, nz, seed, stream, lo=-1.0, hi=1.0):
+    """Values on every cell (halo included), padding columns zero."""
+    f = synth.empty_field(nx, ny, nz)
+    f[:, :, : nx + 2] = synth.uniform(seed, stream, nz * (ny + 2) * (nx + 2), lo, hi).reshape(nz, ny + 2, nx + 2)
+    return f
+
+
+@pytest.mark.parametrize("mode,dtype_name", [("f64", "float64"), ("f32", "float32")])
+@pytest.mark.parametrize("shape", [(37, 13, 6), (64, 8, 3), (5, 3, 2), (33, 9, 1)])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_adjoint_matches_oracle(gpu, oracle_lib, mode, dtype_name, shape, aligned):
+    """Gather-form GPU adjoint vs the oracle's scatter form, every cell the
+    forward reads (halo included). Cotangent halos hold NaN: they must be
+    ignored."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = shape
+    dt = getattr(torch, dtype_name)
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=51)
+    gs = [_raw(nx, ny, nz, 52, s) for s in range(3)]
+    if mode == "f32":
+        u, v, w = (f.astype(np.float32).astype(np.float64) for f in (u, v, w))
+        gs = [g.astype(np.float32).astype(np.float64) for g in gs]
+    co = oracle_lib.coeffs(nz, 50.0, 40.0, dz, rho, rhon)
+    ref = oracle_lib.advect_adjoint(u, v, w, co, nx, ny, *gs)
+    c = pw.make_coeffs(nz, 50.0, 40.0, dz, rho, rhon).to_device()
+    du, dv, dw = (to_device(f, nx, dt, aligned=aligned) for f in (u, v, w))
+    dg = []
+    for g in gs:
+        t = to_device(g, nx, dt, aligned=aligned)
+        t[:, 0, :] = float("nan")
+        t[:, :, 0] = float("nan")
+        dg.append(t)
+    out = pw.advect_adjoint(du, dv, dw, c, nx, ny, *dg, mode=mode)
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    tol = 1e-13 if mode == "f64" else 2e-6
+    for name, got, want in zip(("gu", "gv", "gw"), out, ref):
+        gn = got.double().cpu().numpy()[:, :, : nx + 2]
+        wn = want[:, :, : nx + 2]
+        assert np.all(np.isfinite(gn)), name
+        scale = max(np.max(np.abs(wn)), 1e-300)
+        assert np.max(np.abs(gn - wn)) <= tol * scale, (name, np.max(np.abs(gn - wn)) / scale)
+
+
+def test_adjoint_accumulate(gpu):
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 20, 10, 5
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
+    f = [to_device(a, nx, torch.float64) for a in synth.fields_iid(nx, ny, nz, seed=3)]
+    g = [to_device(_raw(nx, ny, nz, 4, s), nx, torch.float64) for s in range(3)]
+    a = pw.advect_adjoint(*f, c, nx, ny, *g)
+    b = pw.advect_adjoint(*f, c, nx, ny, *g, out=tuple(x.clone() for x in a), accumulate=True)
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert torch.equal(2 * x, y)
+
+
+@pytest.mark.parametrize("mode", ["f64", "f32"])
+def test_dot_product_adjoint_256(gpu, mode):
+    """<J(x) d, y> = <d, J(x)^T y> on the 256 x 256 x 64 workload with the
+    small configuration's winds; J(x) d = (F(x + h d) - F(x - h d)) / 2h is
+    exact for a quadratic map up to rounding. FP64: 1e-12 relative."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    dt = torch.float64 if mode == "f64" else torch.float32
+    nx, ny, nz = 256, 256, 64
+    dz = synth.dz_uniform(nz, 20.0)
+    c = pw.make_coeffs(nz, 50.0, 50.0, dz).to_device()
+    x = [to_device(a, nx, dt) for a in synth.fields_iid(nx, ny, nz, seed=1)]
+    d = [to_device(_raw(nx, ny, nz, 61, s), nx, dt) for s in range(3)]
+    y = [to_device(_raw(nx, ny, nz, 62, s), nx, dt) for s in range(3)]
+    h = 2.0 ** -6
+    fwd = "f64" if mode == "f64" else "f32"
+    fp = pw.advect(*[a + h * b for a, b in zip(x, d)], c, nx, ny, mode=fwd)
+    fm = pw.advect(*[a - h * b for a, b in zip(x, d)], c, nx, ny, mode=fwd)
+    inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
+    lhs = sum(float(((p - m)[inner].double() / (2 * h) * yy[inner].double()).sum()) for p, m, yy in zip(fp, fm, y))
+    g = pw.advect_adjoint(*x, c, nx, ny, *y, mode=mode)
+    rhs = sum(float((gg[:, :, : nx + 2].double() * dd[:, :, : nx + 2].double()).sum()) for gg, dd in zip(g, d))
+    torch.cuda.synchronize()
+    rel = abs(lhs - rhs) / max(abs(lhs), abs(rhs))
+    assert rel <= (1e-12 if mode == "f64" else 1e-4), rel
+
+
+def test_fold_is_transpose_of_fill(gpu):
+    """<fill(x), y> = <x, fold(y)> exactly on integer data."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    for nx, ny, nz in ((17, 9, 3), (1, 1, 2), (2, 5, 1)):
+        x = to_device(_raw(nx, ny, nz, 71, 0, -8, 8).round(), nx, torch.float64)
+        y = to_device(_raw(nx, ny, nz, 72, 0, -8, 8).round(), nx, torch.float64)
+        fx = x.clone()
+        pw.fill_periodic_halo(fx, nx, ny)
+        fy = y.clone()
+        pw.fold_periodic_halo(fy, nx, ny)
+        torch.cuda.synchronize()
+        a = float((fx[:, :, : nx + 2] * y[:, :, : nx + 2]).sum())
+        b = float((x[:, :, : nx + 2] * fy[:, :, : nx + 2]).sum())
+        assert a == b
+        assert float(fy[:, 0, :].abs().sum()) == 0 and float(fy[:, :, 0].abs().sum()) == 0
+
+
+def test_autograd_backward_is_adjoint(gpu):
+    from paper_2107_13500_gb300 import autograd as pa
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 30, 12, 6
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_stretched(nz)).to_device()
+    x = [to_device(a, nx, torch.float64).requires_grad_() for a in synth.fields_iid(nx, ny, nz, seed=8)]
+    y = [to_device(_raw(nx, ny, nz, 9, s), nx, torch.float64) for s in range(3)]
+    inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
+    out = pa.advect(*x, c, nx, ny, "paired")
+    loss = sum((o[inner] * yy[inner]).sum() for o, yy in zip(out, y))
+    grads = torch.autograd.grad(loss, x)
+    ymask = []
+    for yy in y:
+        m = torch.zeros_like(yy)
+        m[inner] = yy[inner]
+        ymask.append(pw.field_like(x[0]).copy_(m))
+    want = pw.advect_adjoint(*[t.detach() for t in x], c, nx, ny, *ymask)
+    for g, wnt in zip(grads, want):
+        assert torch.allclose(g, wnt, rtol=0, atol=1e-13 * float(wnt.abs().max()))
+
+
+def test_rollout_gradient_checkpointed_and_fd(gpu):
+    """20-step forward-Euler rollout (dt = 0.5 s) of the 256 x 256 x 64
+    workload's winds, differentiated with checkpoints every 5 steps: the
+    gradient equals the uncheckpointed one exactly, and a central finite
+    difference with step 1e-6 along a random direction matches it."""
+    from paper_2107_13500_gb300 import autograd as pa
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 256, 256, 64
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
+    x0 = [to_device(a, nx, torch.float64) for a in synth.fields_iid(nx, ny, nz, seed=1)]
+    for t in x0:
+        pw.fill_periodic_halo(t, nx, ny)
+    y = [to_device(_raw(nx, ny, nz, 81, s), nx, torch.float64) for s in range(3)]
+    inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
+
+    def objective(xs, ckpt):
+        out = pa.rollout(*xs, c, nx, ny, 0.5, 20, mode="f64", checkpoint_every=ckpt)
+        return sum((o[inner] * yy[inner]).sum() for o, yy in zip(out, y))
+
+    xs = [t.clone().requires_grad_() for t in x0]
+    g_ck = torch.autograd.grad(objective(xs, 5), xs)
+    xs2 = [t.clone().requires_grad_() for t in x0]
+    g_full = torch.autograd.grad(objective(xs2, 0), xs2)
+    for a, b in zip(g_ck, g_full):
+        assert torch.equal(a, b)
+    d = [to_device(_raw(nx, ny, nz, 82, s), nx, torch.float64) for s in range(3)]
+    for t in d:
+        t[:, 0, :] = 0
+        t[:, ny + 1, :] = 0
+        t[:, :, 0] = 0
+        t[:, :, nx + 1] = 0
+    h = 1e-6
+    with torch.no_grad():
+        jp = float(objective([a + h * b for a, b in zip(x0, d)], 0))
+        jm = float(objective([a - h * b for a, b in zip(x0, d)], 0))
+    fd = (jp - jm) / (2 * h)
+    an = sum(float((g * dd).sum()) for g, dd in zip(g_ck, d))
+    assert abs(fd - an) <= 1e-6 * max(abs(an), 1.0), (fd, an)

@@ -26,13 +26,13 @@ def gpu():
     return torch
 
 
-def _run(gpu, mode, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, oracle_lib=None):
+def _run(gpu, mode, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, oracle_lib=None, aligned=True):
     from paper_2107_13500_gb300 import pw
     torch = gpu
     co = oracle_lib.coeffs(nz, dx, dy, dz, rho, rhon)
     (so, ab) = oracle_lib.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=8)
     c = pw.make_coeffs(nz, dx, dy, dz, rho, rhon).to_device()
-    du, dv, dw = (to_device(f, nx, torch.float64) for f in (u, v, w))
+    du, dv, dw = (to_device(f, nx, torch.float64, aligned=aligned) for f in (u, v, w))
     out = pw.advect(du, dv, dw, c, nx, ny, mode=mode)
     torch.cuda.synchronize()
     assert pw.device_status() == 0
@@ -50,15 +50,17 @@ def test_small_iid_config(gpu, oracle_lib, mode):
     compare_f64(g, o, a, cfg["nx"], cfg["ny"])
 
 
+@pytest.mark.parametrize("aligned", [True, False])
 @pytest.mark.parametrize("mode", F64_MODES)
 @pytest.mark.parametrize("shape", [(37, 13, 5), (33, 9, 7), (100, 17, 11), (31, 7, 3)])
-def test_ragged_stretched_density(gpu, oracle_lib, mode, shape):
-    """Sizes that leave partial tiles in x and y; stretched grid with density."""
+def test_ragged_stretched_density(gpu, oracle_lib, mode, shape, aligned):
+    """Sizes that leave partial tiles in x and y; stretched grid with density;
+    both the 16-byte-aligned interior layout and the general one."""
     nx, ny, nz = shape
     dz = synth.dz_stretched(nz)
     rho, rhon = synth.density_exponential(dz)
     u, v, w = synth.fields_iid(nx, ny, nz, seed=nx * 7 + ny)
-    g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 40.0, 60.0, dz, rho, rhon, oracle_lib)
+    g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 40.0, 60.0, dz, rho, rhon, oracle_lib, aligned)
     compare_f64(g, o, a, nx, ny)
 
 
@@ -112,8 +114,9 @@ def test_full_134m_iid_config(gpu, oracle_lib, mode):
     print("worst (err/A, normwise):", compare_f64(g, o, a, cfg["nx"], cfg["ny"]))
 
 
+@pytest.mark.parametrize("aligned", [True, False])
 @pytest.mark.parametrize("mode", F64_MODES)
-def test_guard_bands_and_halo_untouched(gpu, oracle_lib, mode):
+def test_guard_bands_and_halo_untouched(gpu, oracle_lib, mode, aligned):
     """Outputs live inside a larger buffer filled with a NaN canary: after the
     call every cell outside the interior (halo, row padding, guard bands
     before and after) still holds the canary bit pattern."""
@@ -122,10 +125,10 @@ def test_guard_bands_and_halo_untouched(gpu, oracle_lib, mode):
     nx, ny, nz = 35, 10, 6
     u, v, w = synth.fields_iid(nx, ny, nz, seed=12)
     c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
-    du, dv, dw = (to_device(f, nx, torch.float64) for f in (u, v, w))
+    du, dv, dw = (to_device(f, nx, torch.float64, aligned=aligned) for f in (u, v, w))
     shape = du.shape
     n = du.numel()
-    guard = 4096
+    guard = 4096 + (1 if aligned else 0)
     canary = torch.tensor([0x7FF4DEADBEEF0001], dtype=torch.int64).view(torch.float64)
     bufs, outs = [], []
     for _ in range(3):
@@ -175,9 +178,11 @@ def test_api_rejects_bad_arguments_on_device(gpu):
     with pytest.raises(pw.PWError) as e:
         pw.advect(u, v, w, c, nx, ny, mode="f64", out=(su, su, sw))
     assert e.value.code == pw.PW_EALIAS
-    flat = torch.zeros(u.numel() + 1, dtype=torch.float64, device="cuda")
-    mis = flat[1:].view(u.shape)
+    # u, v, w share one set of TMA box coordinates: a u at another address
+    # phase (mod 16 bytes) than v and w is rejected
+    other = pw.empty_field(nx, ny, nz, aligned=False)
+    assert other.data_ptr() % 16 != v.data_ptr() % 16
     with pytest.raises(pw.PWError) as e:
-        pw.advect(mis, v, w, c, nx, ny, mode="f64", out=(su, sv, sw))
+        pw.advect(other, v, w, c, nx, ny, mode="f64", out=(su, sv, sw))
     assert e.value.code == pw.PW_EINVAL
     assert pw.device_status() == 0

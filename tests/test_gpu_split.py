@@ -29,11 +29,12 @@ def gpu():
     return torch
 
 
-def _split_run(torch, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None):
+def _split_run(torch, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, aligned=True):
     from paper_2107_13500_gb300 import pw
     c = pw.make_coeffs(nz, dx, dy, dz, rho, rhon).to_device()
     dev = [to_device(f, nx, torch.float64) for f in (u, v, w)]
-    fp, means = zip(*(pw.split_field(t, nx, ny) for t in dev))
+    fp, means = zip(*(pw.split_field(t, nx, ny, out=pw.empty_field(nx, ny, nz, torch.float32, aligned=aligned))
+                      for t in dev))
     table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
     out = pw.advect(*fp, c, nx, ny, mode="split", split_table=table)
     torch.cuda.synchronize()
@@ -61,10 +62,10 @@ def split_scale(oracle_lib, fields, means, co, nx, ny):
     return ab
 
 
-def _case(gpu, oracle_lib, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None):
+def _case(gpu, oracle_lib, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, aligned=True):
     co = oracle_lib.coeffs(nz, dx, dy, dz, rho, rhon)
     ref = oracle_lib.advect(u, v, w, co, nx, ny, nthreads=8)
-    g, means, _ = _split_run(gpu, u, v, w, nx, ny, nz, dx, dy, dz, rho, rhon)
+    g, means, _ = _split_run(gpu, u, v, w, nx, ny, nz, dx, dy, dz, rho, rhon, aligned)
     ab = split_scale(oracle_lib, (u, v, w), means, co, nx, ny)
     return _check(g, ref, ab, nx, ny)
 
@@ -75,15 +76,49 @@ def test_split_small_iid(gpu, oracle_lib):
     print(_case(gpu, oracle_lib, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"]))
 
 
-@pytest.mark.parametrize("shape", [(37, 13, 5), (100, 17, 11), (31, 7, 3), (1, 1, 2), (5, 3, 1)])
-def test_split_ragged_modes_density(gpu, oracle_lib, shape):
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("shape", [(37, 13, 5), (100, 17, 11), (31, 7, 3), (1, 1, 2), (5, 3, 1), (66, 9, 6),
+                                   (129, 5, 4)])
+def test_split_ragged_modes_density(gpu, oracle_lib, shape, aligned):
     """Smooth winds with a 5 m/s mean (where the split matters), stretched
-    grid with density, partial tiles, degenerate heights."""
+    grid with density, partial tiles and strips, degenerate heights, both
+    interior alignments."""
     nx, ny, nz = shape
     dz = synth.dz_stretched(nz)
     rho, rhon = synth.density_exponential(dz)
     u, v, w = synth.fields_modes(nx, ny, nz, 50.0, 50.0, dz, seed=nx + ny)
-    _case(gpu, oracle_lib, u, v, w, nx, ny, nz, 50.0, 50.0, dz, rho, rhon)
+    _case(gpu, oracle_lib, u, v, w, nx, ny, nz, 50.0, 50.0, dz, rho, rhon, aligned)
+
+
+@pytest.mark.parametrize("aligned", [True, False])
+def test_split_guard_bands_and_halo_untouched(gpu, aligned):
+    """float outputs inside NaN-canary buffers: nothing outside the interior
+    is written, for the vector (aligned) and scalar store paths."""
+    import torch
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 70, 6, 5
+    u, v, w = synth.fields_modes(nx, ny, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0), seed=4)
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
+    dev = [to_device(f, nx, torch.float64) for f in (u, v, w)]
+    fp, means = zip(*(pw.split_field(t, nx, ny, out=pw.empty_field(nx, ny, nz, torch.float32, aligned=aligned))
+                      for t in dev))
+    table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
+    shape, n = fp[0].shape, fp[0].numel()
+    guard = 2048 + (3 if aligned else 0)
+    canary = 0x7FC0BEEF
+    bufs, outs = [], []
+    for _ in range(3):
+        b = torch.empty(n + 2 * guard, dtype=torch.float32, device="cuda")
+        b.view(torch.int32).fill_(canary)
+        bufs.append(b)
+        outs.append(b[guard:guard + n].view(shape))
+    pw.advect(*fp, c, nx, ny, mode="split", split_table=table, out=tuple(outs))
+    torch.cuda.synchronize()
+    for b in bufs:
+        bits = b.view(torch.int32).cpu().numpy()
+        mask = np.ones(bits.shape, dtype=bool)
+        mask[guard:guard + n].reshape(shape)[:, 1:ny + 1, 1:nx + 1] = False
+        assert np.all(bits[mask] == canary)
 
 
 def test_split_field_means_and_perturbations(gpu):
