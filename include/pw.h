@@ -239,6 +239,35 @@ int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain *doms, int variant
 int pw_advect_batched(pw_dtype dtype, int variant, void *plan_dev, long long n_items, void *stream);
 
 /*
+ * pw_advect_batched_noalloc -- pw_advect_batched for callers that cannot
+ * allocate device memory. (The paper has no counterpart: this is a property
+ * of the library, not of the method.) pw_advect_batched needs the batch plan
+ * in a device buffer the caller allocates; code that is capturing a CUDA
+ * graph, real-time loops that must not call cudaMalloc (it can synchronise
+ * the device), and programs whose device memory is wholly reserved by
+ * another allocator cannot make that buffer. This entry point takes the HOST
+ * plan from pw_make_batch_plan instead and copies it, on `stream`, into a
+ * fixed device array inside the library (room for PW_NOALLOC_MAX_DOMAINS
+ * domains, about 150 KB, which every GPU that loads the library holds until
+ * the process exits), zeroes the work counter there and launches the same
+ * persistent kernel. It calls no cudaMalloc, cudaFree or allocating library
+ * routine. The first call on a device looks up the array's address on that
+ * device (make that call, with the device current, before any stream
+ * capture). Every call on a device shares the one array: calls whose work
+ * overlaps on the GPU race and produce unspecified results, so order them
+ * (same stream, or events). Plans with more than PW_NOALLOC_MAX_DOMAINS
+ * domains are rejected with PW_EINVAL. Its own errors are reported through
+ * pw_noalloc_last_error. Errors: PW_ENULL, PW_EINVAL, PW_EUNSUPPORTED,
+ * PW_ECUDA.
+ */
+#define PW_NOALLOC_MAX_DOMAINS 256
+int pw_advect_batched_noalloc(pw_dtype dtype, int variant, const void *plan_host, size_t plan_bytes,
+                              long long n_items, void *stream);
+
+/* Message for the last failure of pw_advect_batched_noalloc in this thread. */
+const char *pw_noalloc_last_error(void);
+
+/*
  * pw_device_status -- read and clear the library's device error word on the
  * current device (synchronises `stream`). *status receives 0, PW_ETIMEOUT if
  * a kernel gave up on a bounded wait since the last call, or PW_EINVAL if a
