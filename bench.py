@@ -151,6 +151,22 @@ def time_launches(torch, fn, steps, warmup, nsets):
     return start.elapsed_time(end) / steps
 
 
+def replica_throughput(local_ms, points_per_rank, dist=None, device="cpu"):
+    """(max_ms, GPoints/s) of a replicas-only run: every rank evaluated
+    points_per_rank points in local_ms; the job's time is the slowest rank's,
+    its throughput all ranks' points over that time. Without a process group
+    this is the single-GPU figure."""
+    import torch
+    world = 1
+    ms = float(local_ms)
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * points_per_rank / (ms * 1e-3) / 1e9
+
+
 def error_stats(gpu_out, ref, ab, nx, ny):
     out = {}
     for name, g, o, a in zip(("su", "sv", "sw"), gpu_out, ref, ab):
@@ -314,36 +330,44 @@ def main():
     status = pw.device_status()
     if status != 0:
         raise SystemExit(f"kernel reported device status {status}")
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * pts / (ms * 1e-3) / 1e9
+    ms, value = replica_throughput(ms, pts, dist, device="cuda")
 
-    # end to end through the public API: pinned host inputs -> device -> pw_advect -> host outputs
-    host_in = [torch.from_numpy(a).pin_memory() for a in (u_np, v_np, w_np)]
-    host_out = [torch.empty(u_np.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
-    dev_in = [pw.empty_field(nx, ny, nz) for _ in range(3)]
-    dev_out = [pw.empty_field(nx, ny, nz) for _ in range(3)]
+    # end to end through the public API: pinned host inputs -> device ->
+    # pw_advect -> host outputs, inside the timed region. Overlapped form:
+    # pw_advect_host_chunked (y-slab transfers on two streams around the
+    # compute stream); serial form for comparison.
     e2e_mode = mode if mode != "split" else "paired"
+    host_in = [pw.pinned_field(nx, ny, nz) for _ in range(3)]
+    for h, a in zip(host_in, (u_np, v_np, w_np)):
+        h.copy_(torch.from_numpy(a))
+    host_out = tuple(pw.pinned_field(nx, ny, nz) for _ in range(3))
+    pipe = pw.HostPipeline(nx, ny, nz)
+    nchunks = 8
 
     def e2e_step(_):
+        pw.advect_host(*host_in, c, nx, ny, mode=e2e_mode, out_host=host_out, pipeline=pipe, nchunks=nchunks,
+                       wait=False)
+
+    e2e_steps = max(5, min(args.steps // 10, 200))
+    e2e_ms = time_launches(torch, e2e_step, e2e_steps, 3, 1)
+    e2e_ms, e2e_value = replica_throughput(e2e_ms, pts, dist, device="cuda")
+    dev_in, dev_out = pipe.dev[:3], pipe.dev[3:]
+
+    def serial_step(_):
         for d, h in zip(dev_in, host_in):
             d.copy_(h, non_blocking=True)
         pw.advect(*dev_in, c, nx, ny, mode=e2e_mode, out=tuple(dev_out), stream=stream)
         for h, d in zip(host_out, dev_out):
             h.copy_(d, non_blocking=True)
 
-    e2e_steps = max(5, min(args.steps // 10, 200))
-    e2e_ms = time_launches(torch, e2e_step, e2e_steps, 3, 1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    field_bytes = u_np.nbytes
-    e2e = {"value": world * pts / (e2e_ms * 1e-3) / 1e9, "unit": "GPoints/s",
+    serial_ms = time_launches(torch, serial_step, e2e_steps, 3, 1)
+    field_bytes = host_in[0].numel() * host_in[0].element_size()
+    e2e = {"value": e2e_value, "unit": "GPoints/s",
            "h2d_bytes_per_step": 3 * field_bytes, "d2h_bytes_per_step": 3 * field_bytes,
-           "ms_per_step": e2e_ms, "path": f"pinned host -> H2D -> pw_advect({e2e_mode}) -> D2H, one stream"}
+           "ms_per_step": e2e_ms,
+           "path": f"pinned host fields -> pw_advect_host_chunked({e2e_mode}, {nchunks} y-slabs: H2D / compute / "
+                   "D2H streams overlapped) -> pinned host outputs",
+           "serial_ms_per_step": serial_ms, "serial_GPoints_s": pts / (serial_ms * 1e-3) / 1e9}
 
     peak, peak_kind = measured_peaks()
     bpp = pw.BYTES_PER_POINT[mode]
@@ -450,7 +474,96 @@ def extra_modes(torch, pw, oracle, args, sets16, c16, cfg16, ref16, ab16, peak):
     r = res
     r["fp32_split_speedup_over_paired_134m"] = r["134m_split"]["GPoints_s"] / r["134m_paired"]["GPoints_s"]
     r["fp32_split_speedup_over_f64_134m"] = r["134m_split"]["GPoints_s"] / r["134m_f64"]["GPoints_s"]
+    del fp, table
+    torch.cuda.empty_cache()
+    res["batched_96"] = batched_extra(torch, pw)
+    res["adjoint_256"] = adjoint_extra(torch, pw)
     return res
+
+
+def batched_extra(torch, pw):
+    """96 independent domains (x, y in 32..384, z in 32..128, seed 4,
+    stretched grids) in one persistent launch per evaluation: autotuned
+    variant, and a CUDA graph of 50 evaluations."""
+    from paper_2107_13500_gb300 import autotune
+    sizes = synth.batched_domain_sizes(96, seed=4)
+    pts = sum(a * b * c for a, b, c in sizes)
+    out = {"domains": 96, "points": pts}
+    for mode in ("f32", "paired"):
+        dt = torch.float64 if mode == "paired" else torch.float32
+        gen = torch.Generator(device="cuda").manual_seed(4)
+        doms = []
+        for nx, ny, nz in sizes:
+            c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_stretched(nz)).to_device()
+            f = [pw.empty_field(nx, ny, nz, dt) for _ in range(3)]
+            for t in f:
+                t.uniform_(-10, 10, generator=gen)
+            doms.append(dict(u=f[0], v=f[1], w=f[2], nx=nx, ny=ny, coeffs=c))
+        variant, rec = autotune.tune(doms, mode, cache_path=os.path.join(tempfile.gettempdir(), "pw_bench_tune.json"),
+                                     reps=10, force=True)
+        b = pw.Batch(doms, mode, variant)
+        ms = autotune.time_batch(b, reps=50, warmup=5)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            b.run(stream=s)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(50):
+                    b.run(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        graph_ms = e0.elapsed_time(e1) / (3 * 50)
+        bpp = pw.BYTES_PER_POINT[mode]
+        out[mode] = {"variant": variant, "variant_ms": rec["ms"], "ms": ms, "GPoints_s": pts / (ms * 1e-3) / 1e9,
+                     "hbm_frac": bpp * pts / (ms * 1e-3) / 1e9 / measured_peaks()[0],
+                     "graph50_ms_per_eval": graph_ms, "graph50_GPoints_s": pts / (graph_ms * 1e-3) / 1e9}
+        del doms, b, g
+        torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_extra(torch, pw):
+    """256 x 256 x 64 with the small configuration's winds: adjoint kernel
+    time (FP64, FP32) and a 20-step forward-Euler rollout (dt = 0.5 s)
+    differentiated with checkpoints every 5 steps."""
+    from paper_2107_13500_gb300 import autograd as pa
+    nx, ny, nz = 256, 256, 64
+    pts = nx * ny * nz
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=1)
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
+    out = {"points": pts}
+    for mode, dt in (("f64", torch.float64), ("f32", torch.float32)):
+        x = [pw.field_from_numpy(a, nx, dt) for a in (u, v, w)]
+        g = [pw.field_like(x[0]).uniform_(-1, 1) for _ in range(3)]
+        res = tuple(pw.field_like(x[0]) for _ in range(3))
+        ms = time_launches(torch, lambda _: pw.advect_adjoint(*x, c, nx, ny, *g, mode=mode, out=res), 50, 3, 1)
+        out[f"adjoint_{mode}"] = {"ms": ms, "GPoints_s": pts / (ms * 1e-3) / 1e9}
+    x0 = [pw.field_from_numpy(a, nx, torch.float64) for a in (u, v, w)]
+    y = [pw.field_like(x0[0]).uniform_(-1, 1) for _ in range(3)]
+    inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
+
+    def one():
+        xs = [t.clone().requires_grad_() for t in x0]
+        fin = pa.rollout(*xs, c, nx, ny, 0.5, 20, mode="f64", checkpoint_every=5)
+        loss = sum((o[inner] * yy[inner]).sum() for o, yy in zip(fin, y))
+        return torch.autograd.grad(loss, xs)
+
+    one()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    one()
+    torch.cuda.synchronize()
+    out["rollout20_ckpt5_f64_s"] = time.perf_counter() - t0
+    return out
 
 
 if __name__ == "__main__":

@@ -190,6 +190,27 @@ int pw_advect_adjoint(pw_dtype dtype, const void *u, const void *v, const void *
 int pw_fold_periodic_halo(pw_dtype dtype, void *field, const pw_dims *dims, void *stream);
 
 /*
+ * pw_advect_host_chunked -- pw_advect on fields that live in (pinned) host
+ * memory, with the transfers overlapped with the computation (the paper's
+ * Sec. IV chunking of host<->device traffic, here along y). The interior
+ * rows are cut into nchunks slabs; for each slab, in order, the input rows
+ * go host->device on stream_h2d, the slab is computed on stream_compute as
+ * a sub-domain of the device fields (once the next slab's rows, its upper
+ * neighbours, have landed), and its output rows go device->host on
+ * stream_d2h. Each transfer is one strided 2-D copy per field. Host and
+ * device fields share `dims` (same strides); u_d..sw_d are caller-owned
+ * device buffers of the full size. dtype and split as for pw_advect.
+ * Returns after enqueueing; the outputs are in host memory once stream_d2h
+ * reaches its end. Outputs' halo rows and columns are not written.
+ * nchunks is clamped to [1, ny]. Errors: as pw_advect, plus PW_ECUDA from
+ * copies and events.
+ */
+int pw_advect_host_chunked(pw_dtype dtype, const void *u_h, const void *v_h, const void *w_h, void *su_h,
+                           void *sv_h, void *sw_h, void *u_d, void *v_d, void *w_d, void *su_d, void *sv_d,
+                           void *sw_d, const pw_coeffs *c, const pw_dims *dims, const void *split, int nchunks,
+                           void *stream_h2d, void *stream_compute, void *stream_d2h);
+
+/*
  * Batched evaluation: many independent domains of uneven sizes in ONE
  * persistent launch. Every CTA of the launch takes work items (one tile of
  * one domain) from an atomic counter until none are left, so small and
@@ -275,6 +296,17 @@ const char *pw_noalloc_last_error(void);
  * those launches are unspecified). Errors: PW_ENULL, PW_ECUDA.
  */
 int pw_device_status(int *status, void *stream);
+
+/*
+ * pw_selftest_bounded_wait -- exercises the failure path of the bounded
+ * waits every kernel of the library uses: one thread waits on a barrier
+ * that nothing ever completes and must give up after limit_us microseconds
+ * (1..100000), record a timeout and return, leaving the device usable.
+ * Clears the status word first, then stores in *status what
+ * pw_device_status reports afterwards (PW_ETIMEOUT when the bound works).
+ * Synchronises `stream`. Errors: PW_ENULL, PW_EINVAL, PW_ECUDA.
+ */
+int pw_selftest_bounded_wait(unsigned int limit_us, int *status, void *stream);
 
 /* Message for the last failing call in this thread ("" if none). */
 const char *pw_last_error(void);

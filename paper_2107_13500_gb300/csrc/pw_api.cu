@@ -333,6 +333,18 @@ extern "C" int pw_split_field(const double* f, const pw_dims* dims_f, float* fp,
     return PW_OK;
 }
 
+extern "C" int pw_selftest_bounded_wait(unsigned int limit_us, int* status, void* stream) {
+    const char* who = "pw_selftest_bounded_wait";
+    if (!status) return fail(PW_ENULL, "%s: status is NULL", who);
+    if (limit_us < 1 || limit_us > 100000) return fail(PW_EINVAL, "%s: limit_us must be in 1..100000", who);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned int before = 0;
+    cudaError_t e = pw::read_and_clear_status(&before, st);  // start from a clear word
+    if (e == cudaSuccess) e = pw::launch_selftest_wait(1000ull * limit_us, st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return pw_device_status(status, stream);
+}
+
 extern "C" int pw_device_status(int* status, void* stream) {
     if (!status) return fail(PW_ENULL, "pw_device_status: status is NULL");
     unsigned int s = 0;
@@ -490,14 +502,18 @@ extern "C" int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain* doms, 
         a.sw = dm.sw;
         bd.tiles_x = (dm.dims.nx + shp.tx - 1) / shp.tx;
         bd.tiles_y = (dm.dims.ny + shp.ty - 1) / shp.ty;
+        bd.kchunks = 1;  // batches bring enough tiles; each item is a full column
         bd.first_item = items;
-        items += (long long)bd.tiles_x * bd.tiles_y;
+        items += (long long)bd.tiles_x * bd.tiles_y * bd.kchunks;
     }
     plan->counter = 0;
     plan->n_items = items;
     plan->n_domains = n;
     plan->dtype = (int)dtype;
     plan->variant = variant;
+    plan->all_vec = 1;
+    for (int q = 0; q < n; ++q)
+        if (!plan->dom[q].args.vec) plan->all_vec = 0;
     *n_items = items;
     return PW_OK;
 }
@@ -517,6 +533,85 @@ extern "C" int pw_advect_batched(pw_dtype dtype, int variant, void* plan_dev, lo
     if (e != cudaSuccess) return cuda_fail(e, who);
     e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(plan, n_items, st)
                                : pw::launch_split_batched(variant, plan, n_items, st);
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return PW_OK;
+}
+
+// ---------------------------------------------------------------- host overlap
+
+extern "C" int pw_advect_host_chunked(pw_dtype dtype, const void* u_h, const void* v_h, const void* w_h, void* su_h,
+                                      void* sv_h, void* sw_h, void* u_d, void* v_d, void* w_d, void* su_d,
+                                      void* sv_d, void* sw_d, const pw_coeffs* c, const pw_dims* dims,
+                                      const void* split, int nchunks, void* stream_h2d, void* stream_compute,
+                                      void* stream_d2h) {
+    const char* who = "pw_advect_host_chunked";
+    if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
+    const int es = elem_size(dtype);
+    int rc = check_dims(dims, es, who);
+    if (rc) return rc;
+    const void* hp[6] = {u_h, v_h, w_h, su_h, sv_h, sw_h};
+    for (int n = 0; n < 6; ++n)
+        if (!hp[n]) return fail(PW_ENULL, "%s: host field %d is NULL", who, n);
+    const int ny = dims->ny, nz = dims->nz;
+    if (nchunks < 1) nchunks = 1;
+    if (nchunks > ny) nchunks = ny;
+    cudaStream_t sh = static_cast<cudaStream_t>(stream_h2d);
+    cudaStream_t sc = static_cast<cudaStream_t>(stream_compute);
+    cudaStream_t sd = static_cast<cudaStream_t>(stream_d2h);
+    const size_t row = (size_t)dims->sy * es, plane = (size_t)dims->sz * es;
+    // row range [r0, r1] of chunk q (interior rows 1..ny; the first chunk also
+    // carries halo row 0, the last halo row ny+1)
+    auto rows_of = [&](int q, int* r0, int* r1) {
+        *r0 = 1 + (int)((long long)ny * q / nchunks);
+        *r1 = (int)((long long)ny * (q + 1) / nchunks);
+    };
+    std::vector<cudaEvent_t> h2d(nchunks), done(nchunks);
+    cudaError_t e = cudaSuccess;
+    for (int q = 0; q < nchunks && e == cudaSuccess; ++q) {
+        e = cudaEventCreateWithFlags(&h2d[q], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[q], cudaEventDisableTiming);
+    }
+    const void* in_h[3] = {u_h, v_h, w_h};
+    void* in_d[3] = {u_d, v_d, w_d};
+    void* out_h[3] = {su_h, sv_h, sw_h};
+    const void* out_d[3] = {su_d, sv_d, sw_d};
+    // transfers of chunk q's input rows
+    for (int q = 0; q < nchunks && e == cudaSuccess; ++q) {
+        int r0, r1;
+        rows_of(q, &r0, &r1);
+        const int a = (q == 0) ? 0 : r0, b = (q == nchunks - 1) ? ny + 1 : r1;
+        for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+            e = cudaMemcpy2DAsync(static_cast<char*>(in_d[f]) + a * row, plane,
+                                  static_cast<const char*>(in_h[f]) + a * row, plane, (size_t)(b - a + 1) * row, nz,
+                                  cudaMemcpyHostToDevice, sh);
+        if (e == cudaSuccess) e = cudaEventRecord(h2d[q], sh);
+    }
+    // compute chunk q once chunk q+1 (its upper neighbour rows) has landed
+    for (int q = 0; q < nchunks && e == cudaSuccess; ++q) {
+        int r0, r1;
+        rows_of(q, &r0, &r1);
+        e = cudaStreamWaitEvent(sc, h2d[q + 1 < nchunks ? q + 1 : q], 0);
+        if (e != cudaSuccess) break;
+        pw_dims sub = *dims;
+        sub.ny = r1 - r0 + 1;
+        const size_t off = (size_t)(r0 - 1) * row;
+        rc = pw_advect(dtype, static_cast<const char*>(u_d) + off, static_cast<const char*>(v_d) + off,
+                       static_cast<const char*>(w_d) + off, c, &sub, split, static_cast<char*>(su_d) + off,
+                       static_cast<char*>(sv_d) + off, static_cast<char*>(sw_d) + off, sc);
+        if (rc != PW_OK) break;
+        e = cudaEventRecord(done[q], sc);
+        if (e != cudaSuccess) break;
+        e = cudaStreamWaitEvent(sd, done[q], 0);
+        for (int f = 0; f < 3 && e == cudaSuccess; ++f)
+            e = cudaMemcpy2DAsync(static_cast<char*>(out_h[f]) + r0 * row, plane,
+                                  static_cast<const char*>(out_d[f]) + r0 * row, plane, (size_t)(r1 - r0 + 1) * row,
+                                  nz, cudaMemcpyDeviceToHost, sd);
+    }
+    for (int q = 0; q < nchunks; ++q) {
+        if (h2d[q]) cudaEventDestroy(h2d[q]);
+        if (done[q]) cudaEventDestroy(done[q]);
+    }
+    if (rc != PW_OK) return rc;
     if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;
 }

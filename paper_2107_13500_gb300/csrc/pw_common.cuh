@@ -70,15 +70,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase with the given parity to complete, for at most
-// kWaitLimitNs. Returns false on timeout.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+// Second bound on a wait, independent of the timer: try_wait polls.
+constexpr unsigned int kWaitMaxPolls = 1u << 28;
+
+// Wait for the phase with the given parity to complete, for at most limit_ns
+// (and at most kWaitMaxPolls polls). Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    for (unsigned int n = 0; n < kWaitMaxPolls; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > limit_ns) return false;
     }
-    return true;
+    return false;
 }
 
 // 3D tiled TMA load of one box into shared memory, completing on `bar`.

@@ -40,6 +40,8 @@ struct BatchDomain {
     CUtensorMap mu, mv, mw;
     FwdArgs args;
     int tiles_x, tiles_y;
+    int kchunks;      // items per tile: the column is cut into kchunks level ranges
+    int reserved;
     long long first_item;
 };
 
@@ -52,7 +54,7 @@ struct BatchPlan {
     int n_domains;
     int dtype;
     int variant;
-    int reserved;
+    int all_vec;  // every domain takes the 16-byte vector path
     BatchDomain dom[1];
 };
 
@@ -81,6 +83,38 @@ cudaError_t persistent_grid(Kern kern, int threads, int smem, long long n_items,
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
     long long g = (long long)sms * (per_sm > 0 ? per_sm : 1);
     *grid = g < n_items ? g : n_items;
+    return cudaSuccess;
+}
+
+// Level chunks per tile column so that tiles * chunks work units fill the
+// GPU's resident CTA slots in nearly whole waves. Each chunk re-reads one
+// level below and one above, so chunks stay at least 8 levels tall.
+inline int pick_kchunks(long long tiles, int nz, long long slots) {
+    int best = 1;
+    double best_cost = 1e300;
+    for (int c = 1; c <= 8; ++c) {
+        if (c > 1 && nz / c < 8) break;
+        const double units = (double)tiles * c;
+        const double waves = units / (double)slots;
+        const double used = waves / (double)((long long)(waves + 0.999999));  // fraction of the last-wave-rounded time
+        const double extra = (double)(nz + 2 * (c - 1)) / (double)nz;       // re-read and re-split levels
+        const double cost = extra / used;
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
+template <typename Kern>
+cudaError_t choose_kchunks(Kern kern, int threads, int smem, long long tiles, int nz, int* chunks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
+    *chunks = pick_kchunks(tiles, nz, (long long)sms * (per_sm > 0 ? per_sm : 1));
     return cudaSuccess;
 }
 
@@ -119,6 +153,8 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 
 cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, float* fp, long long psy,
                                long long psz, int nx, int ny, int nz, double* mean, cudaStream_t st);
+
+cudaError_t launch_selftest_wait(unsigned long long limit_ns, cudaStream_t st);
 
 // Read and clear the device status words of every kernel unit (synchronises st).
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st);

@@ -240,6 +240,24 @@ cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, fl
 }
 
 // ---------------------------------------------------------------------------
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// ever completes and must give up after limit_ns, recording a timeout.
+
+__global__ void selftest_wait_kernel(unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(&tu_status, kStatusTimeout);
+    }
+}
+
+cudaError_t launch_selftest_wait(unsigned long long limit_ns, cudaStream_t st) {
+    selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st) {
     unsigned int parts[4] = {0, 0, 0, 0};

@@ -121,36 +121,41 @@ __device__ __forceinline__ void st4(float* g, const float* v, int n) {
     }
 }
 
-// One tile: all levels of the TXP x TY columns at tile (bx, by). `seq` is the
-// CTA's running load count (CTA-uniform); it advances by a.nz. Returns false
-// if a bounded wait expired (status set, in-flight loads drained).
+// One tile: output levels kb..ke-1 of the TXP x TY columns at tile (bx, by)
+// (a k-chunk; it reads one level below and one above). `seq` is the CTA's
+// running load count (CTA-uniform); loads are numbered relative to the
+// lowest level read, lo. Returns false if a bounded wait expired (status
+// set, in-flight loads drained).
 template <class Cfg, bool kVec>
 __device__ bool split_tile(SplitRing<Cfg>& ring, const CUtensorMap* mu, const CUtensorMap* mv,
-                           const CUtensorMap* mw, const FwdArgs& a, int bx, int by, long long& seq, int tid) {
+                           const CUtensorMap* mw, const FwdArgs& a, int bx, int by, int kb, int ke, long long& seq,
+                           int tid) {
     constexpr int S = Cfg::S, BX = Cfg::BX, TXP = Cfg::TXP, TY = Cfg::TY;
     const int sx = tid % (TXP / kStrip), ry = tid / (TXP / kStrip);
     const int x0 = bx * TXP, y0 = by * TY;
     const int i0 = x0 + 1 + kStrip * sx, j = y0 + 1 + ry;
     const int nval = (j <= a.ny) ? max(0, min(kStrip, a.nx - i0 + 1)) : 0;
     const int nz = a.nz;
+    const int lo = kb > 0 ? kb - 1 : 0, hi = ke < nz ? ke : nz - 1;
+    const int nl = hi - lo + 1;  // levels read
     const float* table = a.split;
     const long long s0 = seq;
 
-    int issued = 0;
+    int issued = 0;  // relative loads issued (thread 0)
     if (tid == 0) {
         fence_proxy_async_smem();
-        for (; issued < S && issued < nz; ++issued) ring.issue(s0 + issued, issued, mu, mv, mw, table, x0, y0);
+        for (; issued < S && issued < nl; ++issued) ring.issue(s0 + issued, lo + issued, mu, mv, mw, table, x0, y0);
     }
 
     const int cb = (ry + 1) * BX + 1 + a.xoff + kStrip * sx;
     float* __restrict__ su = static_cast<float*>(a.su);
     float* __restrict__ sv = static_cast<float*>(a.sv);
     float* __restrict__ sw = static_cast<float*>(a.sw);
-    size_t g = (size_t)j * (size_t)a.sy + (size_t)i0;
     const size_t gsz = (size_t)a.sz;
+    size_t g = (size_t)j * (size_t)a.sy + (size_t)i0 + (size_t)lo * gsz;
 
     bool bad = !ring.wait(s0);
-    if (nz > 1) bad |= !ring.wait(s0 + 1);
+    if (nl > 1) bad |= !ring.wait(s0 + 1);
     float uo_m[4], vo_m[4], wo_m[4], wx_m[4], wy_m[4], wz_m[4];
     {
         const float* U = ring.box(s0, 0) + cb;
@@ -163,36 +168,37 @@ __device__ bool split_tile(SplitRing<Cfg>& ring, const CUtensorMap* mu, const CU
         w5[4] = W[4];
         float wn[4], wu[4] = {0.f, 0.f, 0.f, 0.f};
         ld4<kVec>(W + BX, wn);
-        if (nz > 1) ld4<kVec>(ring.box(s0 + 1, 2) + cb, wu);
+        if (nl > 1) ld4<kVec>(ring.box(s0 + 1, 2) + cb, wu);
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             wo_m[m] = w5[m];
             wx_m[m] = w5[m] + w5[m + 1];
             wy_m[m] = w5[m] + wn[m];
-            wz_m[m] = nz > 1 ? w5[m] + wu[m] : 0.0f;
+            wz_m[m] = nl > 1 ? w5[m] + wu[m] : 0.0f;
         }
     }
-    if (nval > 0) {
+    if (nval > 0 && kb == 0) {  // level 1 of the paper is not computed
         const float z[4] = {0.f, 0.f, 0.f, 0.f};
         st4<kVec>(su + g, z, nval);
         st4<kVec>(sv + g, z, nval);
         st4<kVec>(sw + g, z, nval);
     }
     bool abort = __syncthreads_or(bad);
-    if (!abort && tid == 0 && issued < nz) {
+    if (!abort && tid == 0 && issued < nl) {
         fence_proxy_async_smem();
-        ring.issue(s0 + issued, issued, mu, mv, mw, table, x0, y0);
+        ring.issue(s0 + issued, lo + issued, mu, mv, mw, table, x0, y0);
         ++issued;
     }
 
-    for (int k = 1; k < nz && !abort; ++k) {
+    for (int k = (kb > 1 ? kb : 1); k < ke && !abort; ++k) {
+        const int r = k - lo;
         g += gsz;
         const bool top = (k == nz - 1);
-        if (!top) bad |= !ring.wait(s0 + k + 1);
-        const float* U = ring.box(s0 + k, 0) + cb;
-        const float* V = ring.box(s0 + k, 1) + cb;
-        const float* W = ring.box(s0 + k, 2) + cb;
-        const float4* T4 = reinterpret_cast<const float4*>(ring.row(s0 + k));
+        if (!top) bad |= !ring.wait(s0 + r + 1);
+        const float* U = ring.box(s0 + r, 0) + cb;
+        const float* V = ring.box(s0 + r, 1) + cb;
+        const float* W = ring.box(s0 + r, 2) + cb;
+        const float4* T4 = reinterpret_cast<const float4*>(ring.row(s0 + r));
 
         // neighbourhoods of the strip: index m+1 is point m, 0 and 5 the x halo
         float uj[6], us[4], un[5], vj[6], vs[5], vn[4], wj[6], ws[4], wn[4];
@@ -215,9 +221,9 @@ __device__ bool split_tile(SplitRing<Cfg>& ring, const CUtensorMap* mu, const CU
         ld4<kVec>(W + BX, wn);
         float uu[5], vu[4], vus[4], wu[4];
         if (!top) {
-            const float* Uu = ring.box(s0 + k + 1, 0) + cb;
-            const float* Vu = ring.box(s0 + k + 1, 1) + cb;
-            const float* Wu = ring.box(s0 + k + 1, 2) + cb;
+            const float* Uu = ring.box(s0 + r + 1, 0) + cb;
+            const float* Vu = ring.box(s0 + r + 1, 1) + cb;
+            const float* Wu = ring.box(s0 + r + 1, 2) + cb;
             uu[0] = Uu[-1];
             ld4<kVec>(Uu, uu + 1);
             ld4<kVec>(Vu, vu);
@@ -277,26 +283,26 @@ __device__ bool split_tile(SplitRing<Cfg>& ring, const CUtensorMap* mu, const CU
             st4<kVec>(sv + g, r_sv, nval);
             st4<kVec>(sw + g, r_sw, nval);
         }
-        abort = __syncthreads_or(bad);  // releases level k's stage
-        if (!abort && tid == 0 && issued < nz) {
+        abort = __syncthreads_or(bad);  // releases relative level r's stage
+        if (!abort && tid == 0 && issued < nl) {
             fence_proxy_async_smem();
-            ring.issue(s0 + issued, issued, mu, mv, mw, table, x0, y0);
+            ring.issue(s0 + issued, lo + issued, mu, mv, mw, table, x0, y0);
             ++issued;
         }
     }
     if (abort) {
         if (tid == 0) {
             atomicOr(&tu_status, kStatusTimeout);
-            for (int lev = (issued > S ? issued - S : 0); lev < issued; ++lev) (void)ring.wait(s0 + lev);
+            for (int q = (issued > S ? issued - S : 0); q < issued; ++q) (void)ring.wait(s0 + q);
         }
         return false;
     }
-    seq = s0 + nz;
+    seq = s0 + nl;
     return true;
 }
 
 template <class Cfg, bool kVec>
-__global__ void __launch_bounds__(Cfg::NT) fwd_split_kernel(const __grid_constant__ CUtensorMap mu,
+__global__ void __launch_bounds__(Cfg::NT, 10) fwd_split_kernel(const __grid_constant__ CUtensorMap mu,
                                                             const __grid_constant__ CUtensorMap mv,
                                                             const __grid_constant__ CUtensorMap mw,
                                                             const FwdArgs a) {
@@ -312,14 +318,41 @@ __global__ void __launch_bounds__(Cfg::NT) fwd_split_kernel(const __grid_constan
     }
     __syncthreads();
     long long seq = 0;
-    (void)split_tile<Cfg, kVec>(ring, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, seq, tid);
+    const int kb = (int)((long long)a.nz * blockIdx.z / gridDim.z);
+    const int ke = (int)((long long)a.nz * (blockIdx.z + 1) / gridDim.z);
+    (void)split_tile<Cfg, kVec>(ring, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid);
 }
 
-// Persistent form: the CTA takes work items (one tile of one domain) from the
-// plan's counter until none are left. Items are ordered by the plan builder
-// (taller columns first). At most n_items iterations.
+// Persistent form: the CTA takes work items (one k-chunk of one tile of one
+// domain) from the plan's counter until none are left; at most n_items
+// iterations. Items are ordered by the plan builder (taller columns first).
+template <class Cfg, bool kVec>
+__device__ __forceinline__ void run_items(BatchPlan* plan, SplitRing<Cfg>& ring, int tid) {
+    const long long n_items = plan->n_items;
+    long long seq = 0;
+    for (long long it = 0; it < n_items; ++it) {
+        if (tid == 0) *ring.item = (long long)atomicAdd(&plan->counter, 1ull);
+        __syncthreads();
+        const long long item = *ring.item;
+        __syncthreads();  // every thread has read the slot before thread 0 rewrites it
+        if (item >= n_items) break;
+        const BatchDomain& d = plan->dom[find_domain(plan, item)];
+        // private copy: the plan is global memory the compiler cannot prove
+        // free of the output stores, so fields read from it would be reloaded
+        const FwdArgs args = d.args;
+        const long long t = item - d.first_item;
+        const int tiles_x = d.tiles_x, kchunks = d.kchunks;
+        const long long tiles = (long long)tiles_x * d.tiles_y;
+        const int ch = (int)(t / tiles), tt = (int)(t % tiles);
+        const int kb = (int)((long long)args.nz * ch / kchunks);
+        const int ke = (int)((long long)args.nz * (ch + 1) / kchunks);
+        if (!split_tile<Cfg, kVec>(ring, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid))
+            break;
+    }
+}
+
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::NT) fwd_split_batched(BatchPlan* plan, int variant) {
+__global__ void __launch_bounds__(Cfg::NT, 8) fwd_split_batched(BatchPlan* plan, int variant) {
     extern __shared__ unsigned char smem_raw[];
     SplitRing<Cfg> ring;
     ring.setup(smem_raw);
@@ -330,21 +363,9 @@ __global__ void __launch_bounds__(Cfg::NT) fwd_split_batched(BatchPlan* plan, in
     }
     if (tid == 0) ring.init_barriers();
     __syncthreads();
-    const long long n_items = plan->n_items;
-    long long seq = 0;
-    for (long long it = 0; it < n_items; ++it) {
-        if (tid == 0) *ring.item = (long long)atomicAdd(&plan->counter, 1ull);
-        __syncthreads();
-        const long long item = *ring.item;
-        __syncthreads();  // every thread has read the slot before thread 0 rewrites it
-        if (item >= n_items) break;
-        const BatchDomain& d = plan->dom[find_domain(plan, item)];
-        const long long t = item - d.first_item;
-        const int bx = (int)(t % d.tiles_x), by = (int)(t / d.tiles_x);
-        const bool ok = d.args.vec ? split_tile<Cfg, true>(ring, &d.mu, &d.mv, &d.mw, d.args, bx, by, seq, tid)
-                                   : split_tile<Cfg, false>(ring, &d.mu, &d.mv, &d.mw, d.args, bx, by, seq, tid);
-        if (!ok) break;
-    }
+    // one whole item loop per path, chosen once, so each gets the registers to itself
+    if (plan->all_vec) run_items<Cfg, true>(plan, ring, tid);
+    else run_items<Cfg, false>(plan, ring, tid);
 }
 
 // Tile-shape / pipeline-depth variants (the autotuner's search space).
@@ -365,7 +386,10 @@ cudaError_t launch_one(const CUtensorMap& mu, const CUtensorMap& mv, const CUten
     auto kern = a.vec ? fwd_split_kernel<Cfg, true> : fwd_split_kernel<Cfg, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.nx + Cfg::TXP - 1) / Cfg::TXP, (a.ny + Cfg::TY - 1) / Cfg::TY);
+    const long long tiles = (long long)((a.nx + Cfg::TXP - 1) / Cfg::TXP) * ((a.ny + Cfg::TY - 1) / Cfg::TY);
+    int chunks = 1;
+    if ((e = choose_kchunks(kern, Cfg::NT, Cfg::SMEM_BYTES, tiles, a.nz, &chunks)) != cudaSuccess) return e;
+    dim3 grid((a.nx + Cfg::TXP - 1) / Cfg::TXP, (a.ny + Cfg::TY - 1) / Cfg::TY, chunks);
     kern<<<grid, Cfg::NT, Cfg::SMEM_BYTES, st>>>(mu, mv, mw, a);
     return cudaGetLastError();
 }

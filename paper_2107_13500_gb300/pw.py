@@ -110,6 +110,12 @@ def load_library(path: str | None = None):
         lib.pw_make_batch_plan.restype = ctypes.c_int
         lib.pw_advect_batched.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_longlong, vp]
         lib.pw_advect_batched.restype = ctypes.c_int
+        lib.pw_advect_host_chunked.argtypes = [ctypes.c_int] + [vp] * 12 + [ctypes.POINTER(Coeffs),
+                                                                          ctypes.POINTER(Dims), vp, ctypes.c_int,
+                                                                          vp, vp, vp]
+        lib.pw_advect_host_chunked.restype = ctypes.c_int
+        lib.pw_selftest_bounded_wait.argtypes = [ctypes.c_uint, ctypes.POINTER(ctypes.c_int), vp]
+        lib.pw_selftest_bounded_wait.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -293,6 +299,61 @@ def advect(u, v, w, coeffs: Coefficients, nx, ny, mode="paired", split_table=Non
     return su, sv, sw
 
 
+class HostPipeline:
+    """Device staging buffers and three streams for advect_host: reuse one
+    across calls on same-shaped fields."""
+
+    def __init__(self, nx, ny, nz, dtype=None, device="cuda"):
+        import torch
+        dtype = dtype or torch.float64
+        self.dev = [empty_field(nx, ny, nz, dtype, device) for _ in range(6)]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(3)]
+
+
+def pinned_field(nx, ny, nz, dtype=None):
+    """Pinned host tensor in the library's layout (for advect_host)."""
+    import torch
+    dtype = dtype or torch.float64
+    es = torch.empty((), dtype=dtype).element_size()
+    return torch.zeros((nz, ny + 2, row_stride(nx, es)), dtype=dtype).pin_memory()
+
+
+def advect_host(u_h, v_h, w_h, coeffs: Coefficients, nx, ny, mode="paired", out_host=None, pipeline=None,
+                nchunks=8, split_table=None, wait=True):
+    """pw_advect on pinned host fields with chunked, overlapped transfers
+    (pw_advect_host_chunked). Returns the host outputs; with wait=True the
+    call returns after they have arrived."""
+    import torch
+    lib = load_library()
+    dt = MODES[mode]
+    nz = u_h.shape[0]
+    d = dims_of(u_h, nx, ny)
+    if pipeline is None:
+        pipeline = HostPipeline(nx, ny, nz, u_h.dtype)
+    if out_host is None:
+        out_host = tuple(torch.zeros_like(u_h).pin_memory() for _ in range(3))
+    if mode == "f32" and split_table is None:
+        split_table = coeffs.zero_mean_table()
+    for t in pipeline.dev:
+        if t.stride() != u_h.stride():
+            raise ValueError("host and device fields must share strides")
+    c = coeffs.c_struct()
+    vp = ctypes.c_void_p
+    sh, sc, sd = pipeline.streams
+    cur = torch.cuda.current_stream()
+    for s in pipeline.streams:
+        s.wait_stream(cur)
+    _check(lib.pw_advect_host_chunked(dt, *(vp(t.data_ptr()) for t in (u_h, v_h, w_h) + tuple(out_host)),
+                                      *(vp(t.data_ptr()) for t in pipeline.dev), ctypes.byref(c), ctypes.byref(d),
+                                      None if split_table is None else vp(split_table.data_ptr()), int(nchunks),
+                                      vp(sh.cuda_stream), vp(sc.cuda_stream), vp(sd.cuda_stream)))
+    for s in pipeline.streams:
+        cur.wait_stream(s)
+    if wait:
+        sd.synchronize()
+    return out_host
+
+
 def split_field(f, nx, ny, out=None, mean=None, stream=None):
     """(fp, mean): float perturbation field and per-level FP64 means of f."""
     import torch
@@ -304,6 +365,14 @@ def split_field(f, nx, ny, out=None, mean=None, stream=None):
     _check(lib.pw_split_field(ctypes.c_void_p(f.data_ptr()), ctypes.byref(df), ctypes.c_void_p(fp.data_ptr()),
                               ctypes.byref(dp), ctypes.c_void_p(m.data_ptr()), _stream_handle(stream)))
     return fp, m
+
+
+def selftest_bounded_wait(limit_us=20000, stream=None) -> int:
+    """Run the bounded-wait self-test; returns the status it left
+    (PW_ETIMEOUT when waits are bounded)."""
+    st = ctypes.c_int(0)
+    _check(load_library().pw_selftest_bounded_wait(int(limit_us), ctypes.byref(st), _stream_handle(stream)))
+    return st.value
 
 
 def device_status(stream=None) -> int:

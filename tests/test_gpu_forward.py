@@ -186,3 +186,45 @@ def test_api_rejects_bad_arguments_on_device(gpu):
         pw.advect(other, v, w, c, nx, ny, mode="f64", out=(su, sv, sw))
     assert e.value.code == pw.PW_EINVAL
     assert pw.device_status() == 0
+
+
+def test_bounded_wait_gives_up_and_device_stays_usable(gpu, oracle_lib):
+    """A kernel waiting on a barrier nothing completes returns after its
+    limit with a timeout status; the device then still runs pw_advect
+    correctly and the status word is clear again."""
+    from paper_2107_13500_gb300 import pw
+    import time
+    t0 = time.perf_counter()
+    assert pw.selftest_bounded_wait(20000) == pw.PW_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert pw.device_status() == 0
+    nx, ny, nz = 20, 9, 5
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=5)
+    g, o, a = _run(gpu, "paired", u, v, w, nx, ny, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0),
+                   oracle_lib=oracle_lib)
+    compare_f64(g, o, a, nx, ny)
+
+
+@pytest.mark.parametrize("mode", ["paired", "f32"])
+@pytest.mark.parametrize("nchunks", [1, 3, 8, 1000])
+def test_host_chunked_matches_device_call(gpu, mode, nchunks):
+    """pw_advect_host_chunked (y-slab transfers overlapped with compute)
+    gives exactly what pw_advect gives on the same data already on the
+    device; host output halos stay untouched."""
+    import torch
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 70, 37, 9
+    dt = torch.float64 if mode == "paired" else torch.float32
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_stretched(nz)).to_device()
+    fields = synth.fields_modes(nx, ny, nz, 50.0, 50.0, synth.dz_stretched(nz), seed=21)
+    host = [pw.pinned_field(nx, ny, nz, dt) for _ in range(3)]
+    for h, a in zip(host, fields):
+        h[:, :, : nx + 2] = torch.from_numpy(a[:, :, : nx + 2]).to(dt)
+    out = tuple(pw.pinned_field(nx, ny, nz, dt).fill_(7.0) for _ in range(3))
+    got = pw.advect_host(*host, c, nx, ny, mode=mode, out_host=out, nchunks=nchunks)
+    dev = [pw.field_from_numpy(a, nx, dt) for a in fields]
+    want = pw.advect(*dev, c, nx, ny, mode=mode)
+    torch.cuda.synchronize()
+    for g, w_ in zip(got, want):
+        assert torch.equal(g[:, 1:ny + 1, 1:nx + 1], w_.cpu()[:, 1:ny + 1, 1:nx + 1])
+        assert float((g[:, 0, :] - 7.0).abs().sum()) == 0.0 and float((g[:, ny + 1, :] - 7.0).abs().sum()) == 0.0
