@@ -43,7 +43,11 @@ WORKLOAD = ("pw_advect su,sv,sw 512x512x64 (16.8M points), FP64 in/out, smooth 8
             "+1% noise, 5 m/s mean wind, dx=dy=50 m, stretched dz=10 m*1.03^(k-2)")
 METRIC = "GPoints/s of su,sv,sw (FP64-accurate, <=1e-13 of the FP64 oracle) and % HBM roofline"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SOURCES = ["pw_paired.cu", "pw_pair.cuh", "pw_ring.cuh", "pw_common.cuh", "pw_kernels.cu", "pw_split.cu"]
+# Sources of each mode's forward kernel: a stored ncu traffic figure is used
+# only while the hash of these files matches the one it was captured with.
+KERNEL_SOURCES = {"paired": ["pw_paired.cu", "pw_pair.cuh", "pw_ring.cuh", "pw_common.cuh"],
+                  "split": ["pw_split.cu", "pw_ring.cuh", "pw_common.cuh"],
+                  "f64": ["pw_kernels.cu", "pw_ring.cuh", "pw_common.cuh"]}
 # Paired-FP32 algorithm, FP32/INT lane operations per point as written: 31 pair
 # sums x 8 + 28 pair products x 4 + 3 double->pair splits x 15 + 3 pair->double
 # joins x 15 (halo re-splits and address/loop work excluded).
@@ -66,9 +70,9 @@ def parse_args():
 
 # ----------------------------------------------------------------------------- helpers
 
-def kernel_source_hash():
+def kernel_source_hash(mode):
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[mode]:
         with open(os.path.join(ROOT, "paper_2107_13500_gb300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -377,7 +381,7 @@ def main():
         with open(PROFILE_TRAFFIC) as fh:
             prof = json.load(fh)
         ent = prof.get(mode)
-        if ent and ent.get("source_hash") == kernel_source_hash():
+        if ent and ent.get("source_hash") == kernel_source_hash(mode):
             traffic = ent.get("bytes_per_launch")
     hbm = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
            "traffic": traffic, "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bpp * pts,
