@@ -89,3 +89,49 @@ __device__ __forceinline__ double pair_to_double(pf a) {
 }
 
 }  // namespace pw
+
+// ---------------------------------------------------------------------------
+// Packed pairs: two independent paired values in the lanes of float2s
+// (h = (h0, h1), l = (l0, l1)), evaluated with the sm_100+ f32x2 add, mul
+// and fma. Each lane rounds exactly as the scalar operations above, so a
+// packed evaluation gives the scalar results bit for bit in half the issued
+// instructions.
+namespace pw {
+
+struct pf2 {
+    float2 h, l;
+};
+
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ pf2 two_sum2(float2 a, float2 b) {
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = __fadd2_rn(s, neg2(a));
+    const float2 e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(bb)))), __fadd2_rn(b, neg2(bb)));
+    return {s, e};
+}
+
+__device__ __forceinline__ pf2 padd2(pf2 a, pf2 b) {
+    pf2 s = two_sum2(a.h, b.h);
+    s.l = __fadd2_rn(s.l, __fadd2_rn(a.l, b.l));
+    return s;
+}
+
+__device__ __forceinline__ pf2 psub2(pf2 a, pf2 b) {
+    pf2 s = two_sum2(a.h, neg2(b.h));
+    s.l = __fadd2_rn(s.l, __fadd2_rn(a.l, neg2(b.l)));
+    return s;
+}
+
+__device__ __forceinline__ pf2 pmul2(pf2 a, pf2 b) {
+    const float2 p = __fmul2_rn(a.h, b.h);
+    float2 e = __ffma2_rn(a.h, b.h, neg2(p));
+    e = __ffma2_rn(a.h, b.l, e);
+    e = __ffma2_rn(a.l, b.h, e);
+    return {p, e};
+}
+
+// The same pair in both lanes.
+__device__ __forceinline__ pf2 dup2(pf a) { return {make_float2(a.h, a.h), make_float2(a.l, a.l)}; }
+
+}  // namespace pw

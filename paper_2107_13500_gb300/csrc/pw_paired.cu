@@ -1,14 +1,23 @@
 // pw_paired.cu -- PW advection with FP64 inputs and outputs and paired-FP32
 // arithmetic (PW_F64_PAIRED).
 //
-// Same k-march as the native kernel: a 3-stage TMA ring brings each level
+// Same k-march as the native kernel: a 2-stage TMA ring brings each level
 // of u, v, w (tile + halo, doubles) into shared memory. Each level is then
 // split once, cooperatively, into (hi, lo) float pairs in a second,
 // three-level shared ring, so neighbouring points do not split the same
-// value again. Step k computes level k from the pairs of levels k and k+1
+// value again; a TMA stage is free again as soon as its level is split.
+// Two stages keep the shared memory at five CTAs per SM. Step k computes level k from the pairs of levels k and k+1
 // plus pairs of level k-1 carried in registers (own-column values and face
 // sums of w), and splits level k+2 for the next step; one CTA barrier per
 // level both publishes level k+2's pairs and frees level k's slot.
+//
+// Each thread evaluates two points of one tile row, A = (x0+1+t, j) and
+// B = A + TX/2 in x, on packed FP32 lanes (pw_pair.cuh: f32x2 add/mul/fma,
+// the same rounding per lane as the scalar form). Because A and B sit at
+// the same offset in the two halves of the tile, every stencil neighbour of
+// the pair is the same offset in both halves: the pair ring interleaves the
+// halves, so one 16-byte read {hA, hB, lA, lB} gives a neighbour of both
+// points already in lane order.
 // Loads are numbered per CTA (`seq`), so the persistent form can run many
 // tiles of many domains through one ring (see pw_ring.cuh).
 #include <cuda.h>
@@ -24,58 +33,96 @@ namespace pw {
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kS = 3, kPL = 3;  // TMA stages, pair-ring levels
+constexpr int kTX = 32, kTY = 8, kS = 2, kPL = 3;  // TMA stages, pair-ring levels
 using Shape = RingShape<double, kTX, kTY, kS>;
-constexpr int kBoxElems = Shape::BX * Shape::BY;
-static_assert(kBoxElems % 2 == 0, "the split pass moves two doubles at a time");
-// pair ring: [kPL levels][3 fields][box] float2, then [kPL levels][4] coefficient pairs
-constexpr int kPairBytes = kPL * 3 * kBoxElems * 8;
-constexpr int kCoefBytes = kPL * 4 * 8;
+constexpr int kHalf = kTX / 2;          // x distance from A to B; threads per tile row
+constexpr int kNT = kHalf * kTY;
+constexpr int kHX = kHalf + 2;          // pair-box row: columns x' = 0..kHalf+1 of both halves
+constexpr int kBoxItems = Shape::BY * kHX;  // float4 {hA, hB, lA, lB} per field and level
+static_assert((kHX - 1) + kHalf + Shape::XOFF_MAX < Shape::BX, "both halves' columns must lie inside the TMA box row");
+// pair ring: [kPL levels][3 fields][kBoxItems] float4, then [kPL levels][4]
+// coefficients as float4 {h, h, l, l}
+constexpr int kPairBytes = kPL * 3 * kBoxItems * 16;
+constexpr int kCoefBytes = kPL * 4 * 16;
 // ring stages | ring barriers (S x 8 B, padded to 64 B) | pairs | coefficient
 // pairs | work-item slot, plus 128 B of slack for aligning the ring base
 constexpr int kPairOffset = Shape::S * Shape::STAGE_BYTES + 64;
 constexpr int kItemOffset = kPairOffset + kPairBytes + kCoefBytes;
 constexpr int kSmemBytes = kItemOffset + 16 + 128;
 static_assert(Shape::S * 8 <= 64, "ring barriers must fit before the pair buffers");
+// A stage is reissued once its level is split, so two stages keep one load
+// in flight while the other level is split.
+static_assert(kS >= 2, "the TMA ring needs a load in flight behind the one being split");
+// CTAs per SM the shared memory allows (1 KB per CTA is reserved by the
+// hardware); the register budget follows from it.
+constexpr int kMinBlocks = (227 * 1024) / (kSmemBytes + 1024);
 
 struct PairSmem {
-    float2* pairs;    // [kPL][3][kBoxElems]
-    float2* coef;     // [kPL][4]: tzc1, tzc2, tzd1, tzd2 of a level
+    float4* pairs;    // [kPL][3][kBoxItems]
+    float4* coef;     // [kPL][4]: tzc1, tzc2, tzd1, tzd2 of a level
     long long* item;  // work item handed from thread 0 to the CTA
-    __device__ __forceinline__ const pf* field(int lev, int f) const {
-        return reinterpret_cast<const pf*>(pairs + ((lev % kPL) * 3 + f) * kBoxElems);
+    __device__ __forceinline__ const float4* field(int lev, int f) const {
+        return pairs + ((lev % kPL) * 3 + f) * kBoxItems;
     }
-    __device__ __forceinline__ pf cf(int lev, int n) const {
-        const float2 c = coef[(lev % kPL) * 4 + n];
-        return {c.x, c.y};
+    __device__ __forceinline__ pf2 cf(int lev, int n) const {
+        const float4 c = coef[(lev % kPL) * 4 + n];
+        return {make_float2(c.x, c.y), make_float2(c.z, c.w)};
     }
 };
 
-// Split load `seq` (level `lev`) into pair slot `slot`, two doubles per
-// 16-byte shared read and two pairs per 16-byte write; threads 0..3 also
-// split the level's four vertical coefficients into the same slot.
+// The split pass gives thread t the items t, t + kNT, ... of a level (item
+// n = (field, row, x') of the pair slot). Which doubles of a stage those are
+// does not depend on the level or the tile, so each thread works out their
+// offsets once.
+constexpr int kConvIters = (3 * kBoxItems + kNT - 1) / kNT;
+static_assert(Shape::BOX_STRIDE % 8 == 0, "box stride in doubles");
+struct ConvPlan {
+    int off[kConvIters];  // offset (doubles) in a stage of lane A's value of item tid + q*kNT, xoff = 0
+};
+
+__device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
+    ConvPlan cp;
+#pragma unroll
+    for (int q = 0; q < kConvIters; ++q) {
+        const int n = tid + q * kNT;
+        const int f = n / kBoxItems, e = n - f * kBoxItems;
+        const int row = e / kHX, xp = e - row * kHX;
+        cp.off[q] = f * (Shape::BOX_STRIDE / 8) + row * Shape::BX + xp;
+    }
+    return cp;
+}
+
+// Split load `seq` (level `lev`) into pair slot `slot`: item (row, x') of a
+// field takes the doubles of columns x0 + x' (lane A) and x0 + x' + kHalf
+// (lane B) of its box. Threads 0..3 also split the level's four vertical
+// coefficients into the same slot.
 __device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, long long seq, int lev,
-                                              int slot, const FwdArgs& a, int tid) {
-    float4* dst = reinterpret_cast<float4*>(ps.pairs + (slot % kPL) * 3 * kBoxElems);
-    for (int f = 0; f < 3; ++f) {
-        const double2* src = reinterpret_cast<const double2*>(ring.template box<double>(seq, f));
-        for (int e = tid; e < kBoxElems / 2; e += Shape::NT) {
-            const double2 d = src[e];
-            const pf p0 = split_double(d.x), p1 = split_double(d.y);
-            dst[f * (kBoxElems / 2) + e] = make_float4(p0.h, p0.l, p1.h, p1.l);
+                                              int slot, const FwdArgs& a, int tid, const ConvPlan& cp) {
+    float4* dst = ps.pairs + (slot % kPL) * 3 * kBoxItems;
+    const double* base = ring.template box<double>(seq, 0) + a.xoff;
+#pragma unroll
+    for (int q = 0; q < kConvIters; ++q) {
+        const int n = tid + q * kNT;
+        if ((q + 1) * kNT <= 3 * kBoxItems || n < 3 * kBoxItems) {
+            const double* src = base + cp.off[q];
+            const pf p0 = split_double(src[0]), p1 = split_double(src[kHalf]);
+            dst[n] = make_float4(p0.h, p1.h, p0.l, p1.l);
         }
     }
     if (tid < 4) {
         const double* arr = tid == 0 ? a.tzc1 : tid == 1 ? a.tzc2 : tid == 2 ? a.tzd1 : a.tzd2;
         const pf p = split_double(__ldg(arr + lev));
-        ps.coef[(slot % kPL) * 4 + tid] = make_float2(p.h, p.l);
+        ps.coef[(slot % kPL) * 4 + tid] = make_float4(p.h, p.h, p.l, p.l);
     }
 }
 
-__device__ __forceinline__ pf ld(const pf* b, int idx) {
-    const float2 v = reinterpret_cast<const float2*>(b)[idx];
-    return {v.x, v.y};
+__device__ __forceinline__ pf2 ld(const float4* b, int idx) {
+    const float4 v = b[idx];
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
+
+__device__ __forceinline__ double join_a(const pf2& p) { return pair_to_double(pf{p.h.x, p.l.x}); }
+__device__ __forceinline__ double join_b(const pf2& p) { return pair_to_double(pf{p.h.y, p.l.y}); }
 
 // One tile (bx, by) of domain `a`, output levels kb..ke-1 (a k-chunk; the
 // chunk reads one level below and one above). `seq` is the CTA's running
@@ -84,12 +131,13 @@ __device__ __forceinline__ pf ld(const pf* b, int idx) {
 // (status set, copies drained).
 __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtensorMap* mu, const CUtensorMap* mv,
                             const CUtensorMap* mw, const FwdArgs& a, int bx, int by, int kb, int ke,
-                            long long& seq, int tid) {
-    constexpr int TX = Shape::TX, S = Shape::S, BX = Shape::BX;
-    const int tx = tid % TX, ty = tid / TX;
-    const int x0 = bx * TX, y0 = by * Shape::TY;
-    const int i = x0 + 1 + tx, j = y0 + 1 + ty;
-    const bool act = (i <= a.nx) && (j <= a.ny);
+                            long long& seq, int tid, const ConvPlan& cp) {
+    constexpr int S = Shape::S;
+    const int tx = tid % kHalf, ty = tid / kHalf;
+    const int x0 = bx * kTX, y0 = by * kTY;
+    const int i = x0 + 1 + tx, j = y0 + 1 + ty;  // point A; B is i + kHalf
+    const bool act_a = (i <= a.nx) && (j <= a.ny);
+    const bool act_b = (i + kHalf <= a.nx) && (j <= a.ny);
     const int nz = a.nz;
     const int lo = kb > 0 ? kb - 1 : 0, hi = ke < nz ? ke : nz - 1;
     const int nl = hi - lo + 1;  // levels read
@@ -101,47 +149,58 @@ __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtenso
         for (; issued < S && issued < nl; ++issued) ring.issue(s0 + issued, lo + issued, mu, mv, mw, x0, y0);
     }
 
-    const pf tcx = split_double(a.tcx), tcy = split_double(a.tcy);
-    const int c0 = (ty + 1) * BX + (tx + 1) + a.xoff;
+    const pf2 tcx = dup2(split_double(a.tcx)), tcy = dup2(split_double(a.tcy));
+    const int c = (ty + 1) * kHX + (tx + 1);  // pair item of (A, B)
     double* __restrict__ su = static_cast<double*>(a.su);
     double* __restrict__ sv = static_cast<double*>(a.sv);
     double* __restrict__ sw = static_cast<double*>(a.sw);
     const size_t gsz = (size_t)a.sz;
     size_t g = (size_t)j * (size_t)a.sy + (size_t)i + (size_t)lo * gsz;
 
-    // Relative levels 0..2 are split up front; the step at relative level r
-    // splits r+2.
+    // Relative levels 0..2 are split up front, each stage reissued as soon
+    // as its level is split; the step at relative level r splits r+2.
     const int pre = nl < kPL ? nl : kPL;
-    bool bad = false;
-    for (int r = 0; r < pre; ++r) {
+    bool bad = false, abort = false;
+    for (int r = 0; r < pre && !abort; ++r) {
         bad |= !ring.wait(s0 + r);
-        convert_level(ring, ps, s0 + r, lo + r, r, a, tid);
-    }
-    bool abort = __syncthreads_or(bad);
-    if (!abort && tid == 0) {
-        fence_proxy_async_smem();
-        for (int n = 0; n < pre && issued < nl; ++n, ++issued) ring.issue(s0 + issued, lo + issued, mu, mv, mw, x0, y0);
+        convert_level(ring, ps, s0 + r, lo + r, r, a, tid, cp);
+        abort = __syncthreads_or(bad);  // load r's stage is free again
+        if (!abort && tid == 0 && issued < nl) {
+            fence_proxy_async_smem();
+            ring.issue(s0 + issued, lo + issued, mu, mv, mw, x0, y0);
+            ++issued;
+        }
     }
 
-    pf uo_m, vo_m, wo_m, wx_m, wy_m, wz_m;
+    pf2 uo_m, vo_m, wo_m, wx_m, wy_m, wz_m;
     {
-        const pf* U = ps.field(0, 0);
-        const pf* V = ps.field(0, 1);
-        const pf* W = ps.field(0, 2);
-        uo_m = ld(U, c0);
-        vo_m = ld(V, c0);
-        wo_m = ld(W, c0);
-        wx_m = padd(wo_m, ld(W, c0 + 1));
-        wy_m = padd(wo_m, ld(W, c0 + BX));
-        wz_m = nl > 1 ? padd(ld(ps.field(1, 2), c0), wo_m) : pf{0.f, 0.f};
+        const float4* U = ps.field(0, 0);
+        const float4* V = ps.field(0, 1);
+        const float4* W = ps.field(0, 2);
+        uo_m = ld(U, c);
+        vo_m = ld(V, c);
+        wo_m = ld(W, c);
+        wx_m = padd2(wo_m, ld(W, c + 1));
+        wy_m = padd2(wo_m, ld(W, c + kHX));
+        wz_m = nl > 1 ? padd2(ld(ps.field(1, 2), c), wo_m) : pf2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     }
-    if (act && kb == 0) {  // level 1 of the paper is not computed
-        su[g] = 0.0;
-        sv[g] = 0.0;
-        sw[g] = 0.0;
+    if (kb == 0) {  // level 1 of the paper is not computed
+        if (act_a) {
+            su[g] = 0.0;
+            sv[g] = 0.0;
+            sw[g] = 0.0;
+        }
+        if (act_b) {
+            su[g + kHalf] = 0.0;
+            sv[g + kHalf] = 0.0;
+            sw[g + kHalf] = 0.0;
+        }
     }
     abort = __syncthreads_or(bad);  // relative slot 0 is rewritten by the first step
 
+    // two levels per unrolled iteration: the level-(k-1) carries swap
+    // registers instead of being copied
+#pragma unroll 2
     for (int k = (kb > 1 ? kb : 1); k < ke && !abort; ++k) {
         const int r = k - lo;
         g += gsz;
@@ -149,49 +208,55 @@ __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtenso
         if (r + 2 < nl) {
             // split relative level r+2 into the slot of r-1 (freed by the last barrier)
             bad |= !ring.wait(s0 + r + 2);
-            convert_level(ring, ps, s0 + r + 2, k + 2, r + 2, a, tid);
+            convert_level(ring, ps, s0 + r + 2, k + 2, r + 2, a, tid, cp);
         }
-        const pf* U = ps.field(r, 0);
-        const pf* V = ps.field(r, 1);
-        const pf* W = ps.field(r, 2);
-        const pf uc = ld(U, c0), uw = ld(U, c0 - 1), ue = ld(U, c0 + 1), us = ld(U, c0 - BX), un = ld(U, c0 + BX);
-        const pf unw = ld(U, c0 + BX - 1);
-        const pf vc = ld(V, c0), vw = ld(V, c0 - 1), ve = ld(V, c0 + 1), vs = ld(V, c0 - BX), vn = ld(V, c0 + BX);
-        const pf vse = ld(V, c0 - BX + 1);
-        const pf wc = ld(W, c0), ww = ld(W, c0 - 1), we = ld(W, c0 + 1), ws = ld(W, c0 - BX), wn = ld(W, c0 + BX);
-        const pf tz1 = ps.cf(r, 0), tz2 = ps.cf(r, 1);
+        const float4* U = ps.field(r, 0);
+        const float4* V = ps.field(r, 1);
+        const float4* W = ps.field(r, 2);
+        const pf2 uc = ld(U, c), uw = ld(U, c - 1), ue = ld(U, c + 1), us = ld(U, c - kHX), un = ld(U, c + kHX);
+        const pf2 unw = ld(U, c + kHX - 1);
+        const pf2 vc = ld(V, c), vw = ld(V, c - 1), ve = ld(V, c + 1), vs = ld(V, c - kHX), vn = ld(V, c + kHX);
+        const pf2 vse = ld(V, c - kHX + 1);
+        const pf2 wc = ld(W, c), ww = ld(W, c - 1), we = ld(W, c + 1), ws = ld(W, c - kHX), wn = ld(W, c + kHX);
+        const pf2 tz1 = ps.cf(r, 0), tz2 = ps.cf(r, 1);
 
         // su: tcx (a-c)(a+b+c) + tcy [u(j-1) V(j-1) - u(j+1) V(j)] + tzc1 u(k-1) W(k-1) - tzc2 u(k+1) W(k)
-        pf r_su = pmul(tcx, pmul(psub(uw, ue), padd(padd(uw, uc), ue)));
-        r_su = padd(r_su, pmul(tcy, psub(pmul(us, padd(vs, vse)), pmul(un, padd(vc, ve)))));
-        r_su = padd(r_su, pmul(tz1, pmul(uo_m, wx_m)));
+        pf2 r_su = pmul2(tcx, pmul2(psub2(uw, ue), padd2(padd2(uw, uc), ue)));
+        r_su = padd2(r_su, pmul2(tcy, psub2(pmul2(us, padd2(vs, vse)), pmul2(un, padd2(vc, ve)))));
+        r_su = padd2(r_su, pmul2(tz1, pmul2(uo_m, wx_m)));
         // sv: mirror of su in x and y
-        pf r_sv = pmul(tcy, pmul(psub(vs, vn), padd(padd(vs, vc), vn)));
-        r_sv = padd(r_sv, pmul(tcx, psub(pmul(vw, padd(uw, unw)), pmul(ve, padd(uc, un)))));
-        r_sv = padd(r_sv, pmul(tz1, pmul(vo_m, wy_m)));
-        const pf wx = padd(wc, we), wy = padd(wc, wn);
-        double d_sw = 0.0;
-        pf wz = {0.f, 0.f};
+        pf2 r_sv = pmul2(tcy, pmul2(psub2(vs, vn), padd2(padd2(vs, vc), vn)));
+        r_sv = padd2(r_sv, pmul2(tcx, psub2(pmul2(vw, padd2(uw, unw)), pmul2(ve, padd2(uc, un)))));
+        r_sv = padd2(r_sv, pmul2(tz1, pmul2(vo_m, wy_m)));
+        const pf2 wx = padd2(wc, we), wy = padd2(wc, wn);
+        double sw_a = 0.0, sw_b = 0.0;
+        pf2 wz = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         if (!top) {
-            const pf* Uu = ps.field(r + 1, 0);
-            const pf* Vu = ps.field(r + 1, 1);
-            const pf* Wu = ps.field(r + 1, 2);
-            const pf uu = ld(Uu, c0), uuw = ld(Uu, c0 - 1);
-            const pf vu = ld(Vu, c0), vus = ld(Vu, c0 - BX);
-            const pf wu = ld(Wu, c0);
-            const pf td1 = ps.cf(r, 2), td2 = ps.cf(r, 3);
-            r_su = psub(r_su, pmul(tz2, pmul(uu, wx)));
-            r_sv = psub(r_sv, pmul(tz2, pmul(vu, wy)));
-            wz = padd(wc, wu);
-            pf r_sw = pmul(tcx, psub(pmul(ww, padd(uw, uuw)), pmul(we, padd(uc, uu))));
-            r_sw = padd(r_sw, pmul(tcy, psub(pmul(ws, padd(vs, vus)), pmul(wn, padd(vc, vu)))));
-            r_sw = padd(r_sw, psub(pmul(td1, pmul(wo_m, wz_m)), pmul(td2, pmul(wu, wz))));
-            d_sw = pair_to_double(r_sw);
+            const float4* Uu = ps.field(r + 1, 0);
+            const float4* Vu = ps.field(r + 1, 1);
+            const float4* Wu = ps.field(r + 1, 2);
+            const pf2 uu = ld(Uu, c), uuw = ld(Uu, c - 1);
+            const pf2 vu = ld(Vu, c), vus = ld(Vu, c - kHX);
+            const pf2 wu = ld(Wu, c);
+            const pf2 td1 = ps.cf(r, 2), td2 = ps.cf(r, 3);
+            r_su = psub2(r_su, pmul2(tz2, pmul2(uu, wx)));
+            r_sv = psub2(r_sv, pmul2(tz2, pmul2(vu, wy)));
+            wz = padd2(wc, wu);
+            pf2 r_sw = pmul2(tcx, psub2(pmul2(ww, padd2(uw, uuw)), pmul2(we, padd2(uc, uu))));
+            r_sw = padd2(r_sw, pmul2(tcy, psub2(pmul2(ws, padd2(vs, vus)), pmul2(wn, padd2(vc, vu)))));
+            r_sw = padd2(r_sw, psub2(pmul2(td1, pmul2(wo_m, wz_m)), pmul2(td2, pmul2(wu, wz))));
+            sw_a = join_a(r_sw);
+            sw_b = join_b(r_sw);
         }
-        if (act) {
-            su[g] = pair_to_double(r_su);
-            sv[g] = pair_to_double(r_sv);
-            sw[g] = d_sw;
+        if (act_a) {
+            su[g] = join_a(r_su);
+            sv[g] = join_a(r_sv);
+            sw[g] = sw_a;
+        }
+        if (act_b) {
+            su[g + kHalf] = join_b(r_su);
+            sv[g + kHalf] = join_b(r_sv);
+            sw[g + kHalf] = sw_b;
         }
         uo_m = uc;
         vo_m = vc;
@@ -220,12 +285,12 @@ __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtenso
 
 __device__ __forceinline__ void setup_smem(unsigned char* raw, Ring<Shape>& ring, PairSmem& ps) {
     ring.setup(raw);
-    ps.pairs = reinterpret_cast<float2*>(ring.base + kPairOffset);
-    ps.coef = ps.pairs + kPL * 3 * kBoxElems;
+    ps.pairs = reinterpret_cast<float4*>(ring.base + kPairOffset);
+    ps.coef = ps.pairs + kPL * 3 * kBoxItems;
     ps.item = reinterpret_cast<long long*>(ring.base + kItemOffset);
 }
 
-__global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
+__global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
                                                                const __grid_constant__ CUtensorMap mv,
                                                                const __grid_constant__ CUtensorMap mw,
                                                                const FwdArgs a) {
@@ -244,12 +309,13 @@ __global__ void __launch_bounds__(Shape::NT) fwd_paired_kernel(const __grid_cons
     long long seq = 0;
     const int kb = (int)((long long)a.nz * blockIdx.z / gridDim.z);
     const int ke = (int)((long long)a.nz * (blockIdx.z + 1) / gridDim.z);
-    (void)paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid);
+    const ConvPlan cp = make_conv_plan(tid);
+    (void)paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid, cp);
 }
 
 // Persistent form over a batch plan: work items (one tile of one domain)
 // come from the plan's counter, at most n_items iterations.
-__global__ void __launch_bounds__(Shape::NT) fwd_paired_batched(BatchPlan* plan) {
+__global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_batched(BatchPlan* plan) {
     extern __shared__ unsigned char smem_raw[];
     Ring<Shape> ring;
     PairSmem ps;
@@ -262,6 +328,7 @@ __global__ void __launch_bounds__(Shape::NT) fwd_paired_batched(BatchPlan* plan)
     if (tid == 0) ring.init_barriers();
     __syncthreads();
     const long long n_items = plan->n_items;
+    const ConvPlan cp = make_conv_plan(tid);
     long long seq = 0;
     for (long long it = 0; it < n_items; ++it) {
         if (tid == 0) *ps.item = (long long)atomicAdd(&plan->counter, 1ull);
@@ -278,7 +345,7 @@ __global__ void __launch_bounds__(Shape::NT) fwd_paired_batched(BatchPlan* plan)
         const int ch = (int)(t / tiles), tt = (int)(t % tiles);
         const int kb = (int)((long long)args.nz * ch / kchunks);
         const int ke = (int)((long long)args.nz * (ch + 1) / kchunks);
-        if (!paired_tile(ring, ps, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid)) break;
+        if (!paired_tile(ring, ps, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid, cp)) break;
     }
 }
 
@@ -288,7 +355,7 @@ cudaError_t read_and_clear_status_paired(unsigned int* status, cudaStream_t st) 
     return read_and_clear_tu_status(status, st);
 }
 
-TileShape fwd_paired_shape() { return TileShape{kTX, kTY, Shape::BX, Shape::BY, kSmemBytes, Shape::NT}; }
+TileShape fwd_paired_shape() { return TileShape{kTX, kTY, Shape::BX, Shape::BY, kSmemBytes, kNT}; }
 
 cudaError_t launch_fwd_paired(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                               const FwdArgs& a, cudaStream_t st) {
@@ -296,9 +363,9 @@ cudaError_t launch_fwd_paired(const CUtensorMap& mu, const CUtensorMap& mv, cons
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY);
     int chunks = 1;
-    if ((e = choose_kchunks(fwd_paired_kernel, Shape::NT, kSmemBytes, tiles, a.nz, &chunks)) != cudaSuccess) return e;
+    if ((e = choose_kchunks(fwd_paired_kernel, kNT, kSmemBytes, tiles, a.nz, &chunks)) != cudaSuccess) return e;
     dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY, chunks);
-    fwd_paired_kernel<<<grid, Shape::NT, kSmemBytes, st>>>(mu, mv, mw, a);
+    fwd_paired_kernel<<<grid, kNT, kSmemBytes, st>>>(mu, mv, mw, a);
     return cudaGetLastError();
 }
 
@@ -307,9 +374,9 @@ cudaError_t launch_paired_batched(BatchPlan* plan, long long n_items, cudaStream
         cudaFuncSetAttribute(fwd_paired_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e != cudaSuccess) return e;
     long long grid = 0;
-    if ((e = persistent_grid(fwd_paired_batched, Shape::NT, kSmemBytes, n_items, &grid)) != cudaSuccess) return e;
+    if ((e = persistent_grid(fwd_paired_batched, kNT, kSmemBytes, n_items, &grid)) != cudaSuccess) return e;
     if (grid < 1) return cudaSuccess;
-    fwd_paired_batched<<<(unsigned)grid, Shape::NT, kSmemBytes, st>>>(plan);
+    fwd_paired_batched<<<(unsigned)grid, kNT, kSmemBytes, st>>>(plan);
     return cudaGetLastError();
 }
 
