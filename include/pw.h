@@ -229,8 +229,9 @@ size_t pw_batch_plan_bytes(int n);
 
 /* Number of kernel variants (tile shape x pipeline depth) for dtype; variant
  * indices 0 .. count-1 are accepted by pw_make_batch_plan, 0 is the default.
- * PW_F32 / PW_F32_SPLIT: 0 = 64x4 points per CTA, 4-level ring; 1 = 32x8;
- * 2 = 128x2; 3 = 64x4 with a 3-level ring; 4 = 64x4 with a 6-level ring.
+ * PW_F32 / PW_F32_SPLIT (points per CTA, TMA ring depth): 0 = 128x4, 4 levels;
+ * 1 = 64x4; 2 = 32x8; 3 = 64x8; 4 = 32x16; 5 = 128x2 (all 4 levels);
+ * 6 = 64x4, 3 levels; 7 = 64x4, 6 levels.
  * PW_F64_PAIRED: 1 variant. PW_F64: 0 (not batched). */
 int pw_variant_count(pw_dtype dtype);
 

@@ -2,9 +2,10 @@
 and TMA pipeline depth, see pw_variant_count in include/pw.h) by timing each
 on the batch itself, and caches the winner per shape class in a JSON file.
 
-Shape class of a batch: arithmetic mode, number of domains, and the domains'
-sizes rounded to powers of two (x, y, z) as a sorted histogram, so batches
-with similar geometry reuse one measurement.
+Shape class of a batch: library version (variant numbering belongs to it),
+arithmetic mode, number of domains, and the domains' sizes rounded to powers
+of two (x, y, z) as a sorted histogram, so batches with similar geometry
+reuse one measurement.
 """
 from __future__ import annotations
 
@@ -33,7 +34,7 @@ def shape_class(mode: str, domains) -> str:
         key = (_p2(d["nx"]), _p2(d["ny"]), _p2(d["u"].shape[0]))
         hist[key] = hist.get(key, 0) + 1
     parts = ",".join(f"{x}x{y}x{z}:{c}" for (x, y, z), c in sorted(hist.items()))
-    return f"{mode}|n={len(domains)}|{parts}"
+    return f"{pw.version()}|{mode}|n={len(domains)}|{parts}"
 
 
 def _load(path):

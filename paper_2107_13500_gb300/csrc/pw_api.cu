@@ -124,7 +124,7 @@ bool known_dtype(pw_dtype d) { return d == PW_F64 || d == PW_F32_SPLIT || d == P
 
 extern "C" const char* pw_last_error(void) { return t_last_error.c_str(); }
 
-extern "C" const char* pw_version(void) { return "pw-gb300 0.1 (sm_103a)"; }
+extern "C" const char* pw_version(void) { return "pw-gb300 0.2 (sm_103a)"; }
 
 extern "C" int pw_make_coeffs(int nz, double dx, double dy, const double* dz, const double* rho,
                               const double* rhon, double* tc2_host, double* tz4_host) {

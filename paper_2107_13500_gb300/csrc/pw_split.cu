@@ -31,10 +31,17 @@ namespace {
 constexpr int kStrip = 4;
 constexpr int kRowBytes = PW_SPLIT_NCOEF * 4;
 
+// Resident warps per SM the one-shot and the persistent kernels are
+// compiled for, whatever the CTA size (the register budget follows).
+constexpr int kWarpsOneShot = 20, kWarpsBatched = 16;
+
 template <int TXP_, int TY_, int S_>
 struct SplitCfg {
     static constexpr int TXP = TXP_, TY = TY_, S = S_;
     static constexpr int NT = (TXP / kStrip) * TY;
+    static constexpr int MIN_BLOCKS = kWarpsOneShot * 32 / NT;
+    static constexpr int MIN_BLOCKS_BATCHED = kWarpsBatched * 32 / NT;
+    static_assert(NT % 32 == 0, "whole warps per CTA");
     using Shape = RingShape<float, TXP, TY, S>;
     static constexpr int BX = Shape::BX;
     static constexpr int STAGE_BYTES = Shape::STAGE_BYTES;
@@ -302,7 +309,7 @@ __device__ bool split_tile(SplitRing<Cfg>& ring, const CUtensorMap* mu, const CU
 }
 
 template <class Cfg, bool kVec>
-__global__ void __launch_bounds__(Cfg::NT, 10) fwd_split_kernel(const __grid_constant__ CUtensorMap mu,
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS) fwd_split_kernel(const __grid_constant__ CUtensorMap mu,
                                                             const __grid_constant__ CUtensorMap mv,
                                                             const __grid_constant__ CUtensorMap mw,
                                                             const FwdArgs a) {
@@ -352,7 +359,7 @@ __device__ __forceinline__ void run_items(BatchPlan* plan, SplitRing<Cfg>& ring,
 }
 
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::NT, 8) fwd_split_batched(BatchPlan* plan, int variant) {
+__global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS_BATCHED) fwd_split_batched(BatchPlan* plan, int variant) {
     extern __shared__ unsigned char smem_raw[];
     SplitRing<Cfg> ring;
     ring.setup(smem_raw);
@@ -369,11 +376,14 @@ __global__ void __launch_bounds__(Cfg::NT, 8) fwd_split_batched(BatchPlan* plan,
 }
 
 // Tile-shape / pipeline-depth variants (the autotuner's search space).
-using V0 = SplitCfg<64, 4, 4>;
-using V1 = SplitCfg<32, 8, 4>;
-using V2 = SplitCfg<128, 2, 4>;
-using V3 = SplitCfg<64, 4, 3>;
-using V4 = SplitCfg<64, 4, 6>;
+using V0 = SplitCfg<128, 4, 4>;
+using V1 = SplitCfg<64, 4, 4>;
+using V2 = SplitCfg<32, 8, 4>;
+using V3 = SplitCfg<64, 8, 4>;
+using V4 = SplitCfg<32, 16, 4>;
+using V5 = SplitCfg<128, 2, 4>;
+using V6 = SplitCfg<64, 4, 3>;
+using V7 = SplitCfg<64, 4, 6>;
 
 template <class Cfg>
 TileShape shape_of() {
@@ -412,7 +422,7 @@ cudaError_t read_and_clear_status_split(unsigned int* status, cudaStream_t st) {
     return read_and_clear_tu_status(status, st);
 }
 
-int split_variant_count() { return 5; }
+int split_variant_count() { return 8; }
 
 TileShape fwd_split_shape_variant(int v) {
     switch (v) {
@@ -420,6 +430,9 @@ TileShape fwd_split_shape_variant(int v) {
         case 2: return shape_of<V2>();
         case 3: return shape_of<V3>();
         case 4: return shape_of<V4>();
+        case 5: return shape_of<V5>();
+        case 6: return shape_of<V6>();
+        case 7: return shape_of<V7>();
         default: return shape_of<V0>();
     }
 }
@@ -433,6 +446,9 @@ cudaError_t launch_fwd_split_variant(int v, const CUtensorMap& mu, const CUtenso
         case 2: return launch_one<V2>(mu, mv, mw, a, st);
         case 3: return launch_one<V3>(mu, mv, mw, a, st);
         case 4: return launch_one<V4>(mu, mv, mw, a, st);
+        case 5: return launch_one<V5>(mu, mv, mw, a, st);
+        case 6: return launch_one<V6>(mu, mv, mw, a, st);
+        case 7: return launch_one<V7>(mu, mv, mw, a, st);
         default: return launch_one<V0>(mu, mv, mw, a, st);
     }
 }
@@ -448,6 +464,9 @@ cudaError_t launch_split_batched(int v, BatchPlan* plan, long long n_items, cuda
         case 2: return launch_batched_cfg<V2>(2, plan, n_items, st);
         case 3: return launch_batched_cfg<V3>(3, plan, n_items, st);
         case 4: return launch_batched_cfg<V4>(4, plan, n_items, st);
+        case 5: return launch_batched_cfg<V5>(5, plan, n_items, st);
+        case 6: return launch_batched_cfg<V6>(6, plan, n_items, st);
+        case 7: return launch_batched_cfg<V7>(7, plan, n_items, st);
         default: return launch_batched_cfg<V0>(0, plan, n_items, st);
     }
 }

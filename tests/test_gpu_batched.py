@@ -162,11 +162,13 @@ def test_batched_plan_variant_mismatch_reported(gpu):
 
 
 def test_autotuner_caches_per_shape_class(gpu, tmp_path):
-    from paper_2107_13500_gb300 import autotune
+    from paper_2107_13500_gb300 import autotune, pw
     torch = gpu
     doms = _domains(torch, SMALL[:4], "split")
     path = str(tmp_path / "tune.json")
     v, rec = autotune.tune(doms, "split", cache_path=path, reps=2)
-    assert 0 <= v < 5 and len(rec["ms"]) == 5
+    nv = pw.variant_count("split")
+    assert nv == 8
+    assert 0 <= v < nv and len(rec["ms"]) == nv
     v2, rec2 = autotune.tune(doms, "split", cache_path=path, reps=2)
     assert v2 == v and rec2 == rec
