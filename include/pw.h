@@ -192,18 +192,20 @@ int pw_fold_periodic_halo(pw_dtype dtype, void *field, const pw_dims *dims, void
 /*
  * pw_advect_host_chunked -- pw_advect on fields that live in (pinned) host
  * memory, with the transfers overlapped with the computation (the paper's
- * Sec. IV chunking of host<->device traffic, here along y). The interior
- * rows are cut into nchunks slabs; for each slab, in order, the input rows
- * go host->device on stream_h2d, the slab is computed on stream_compute as
- * a sub-domain of the device fields (once the next slab's rows, its upper
- * neighbours, have landed), and its output rows go device->host on
- * stream_d2h. Each transfer is one strided 2-D copy per field. Host and
- * device fields share `dims` (same strides); u_d..sw_d are caller-owned
- * device buffers of the full size. dtype and split as for pw_advect.
- * Returns after enqueueing; the outputs are in host memory once stream_d2h
- * reaches its end. Outputs' halo rows and columns are not written.
- * nchunks is clamped to [1, ny]. Errors: as pw_advect, plus PW_ECUDA from
- * copies and events.
+ * Sec. IV chunking of host<->device traffic, here in slabs of levels). The
+ * levels are cut into nchunks slabs; for each slab, in order, its level
+ * planes of u, v, w go host->device on stream_h2d (one contiguous copy per
+ * field), its levels are computed on stream_compute (once the next slab,
+ * which holds their upper neighbour level, has landed), and rows 1..ny of
+ * its output levels go device->host on stream_d2h (one 2-D copy per field,
+ * a row of ny*sy elements per level). Host and device fields share `dims`
+ * (same strides); u_d..sw_d are caller-owned device buffers of the full
+ * size. dtype and split as for pw_advect. Returns after enqueueing; the
+ * outputs are in host memory once stream_d2h reaches its end. The host
+ * outputs' halo rows 0 and ny+1 are not written; their halo columns in rows
+ * 1..ny receive what the device outputs hold there (pw_advect never writes
+ * them). nchunks is clamped to [1, nz]. Errors: as pw_advect, plus
+ * PW_ECUDA from copies and events.
  */
 int pw_advect_host_chunked(pw_dtype dtype, const void *u_h, const void *v_h, const void *w_h, void *su_h,
                            void *sv_h, void *sw_h, void *u_d, void *v_d, void *w_d, void *su_d, void *sv_d,

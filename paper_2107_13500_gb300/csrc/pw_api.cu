@@ -236,9 +236,13 @@ extern "C" int pw_fill_periodic_halo(pw_dtype dtype, void* field, const pw_dims*
     return PW_OK;
 }
 
-extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const void* w, const pw_coeffs* c,
-                         const pw_dims* dims, const void* split, void* su, void* sv, void* sw, void* stream) {
-    const char* who = "pw_advect";
+// pw_advect restricted to output levels k0..k1-1 (0 <= k0 < k1 <= nz) of the
+// full-depth domain `dims`: level k0-1 and level k1 (where they exist) are
+// read as neighbours, and the paper's bottom and top levels keep their
+// treatment. Validation as pw_advect.
+static int advect_levels(pw_dtype dtype, const void* u, const void* v, const void* w, const pw_coeffs* c,
+                         const pw_dims* dims, const void* split, void* su, void* sv, void* sw, void* stream, int k0,
+                         int k1, const char* who) {
     if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
     const int es = elem_size(dtype);
     int rc = check_dims(dims, es, who);
@@ -290,6 +294,10 @@ extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const voi
     a.nx = dims->nx;
     a.ny = dims->ny;
     a.nz = dims->nz;
+    if (k0 < 0 || k1 > dims->nz || k0 >= k1)
+        return fail(PW_EINVAL, "%s: level range [%d, %d) outside [0, %d)", who, k0, k1, dims->nz);
+    a.kbeg = k0;
+    a.kend = k1;
     a.sy = dims->sy;
     a.sz = dims->sz;
     a.tcx = c->tcx;
@@ -311,6 +319,12 @@ extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const voi
     }
     if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;
+}
+
+extern "C" int pw_advect(pw_dtype dtype, const void* u, const void* v, const void* w, const pw_coeffs* c,
+                         const pw_dims* dims, const void* split, void* su, void* sv, void* sw, void* stream) {
+    if (!dims) return fail(PW_ENULL, "pw_advect: dims is NULL");
+    return advect_levels(dtype, u, v, w, c, dims, split, su, sv, sw, stream, 0, dims->nz, "pw_advect");
 }
 
 extern "C" int pw_split_field(const double* f, const pw_dims* dims_f, float* fp, const pw_dims* dims_p,
@@ -484,6 +498,8 @@ extern "C" int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain* doms, 
         a.nx = dm.dims.nx;
         a.ny = dm.dims.ny;
         a.nz = dm.dims.nz;
+        a.kbeg = 0;
+        a.kend = dm.dims.nz;
         a.sy = dm.dims.sy;
         a.sz = dm.dims.sz;
         a.xoff = (int)(((uintptr_t)dm.u % 16) / es);
@@ -554,16 +570,16 @@ extern "C" int pw_advect_host_chunked(pw_dtype dtype, const void* u_h, const voi
         if (!hp[n]) return fail(PW_ENULL, "%s: host field %d is NULL", who, n);
     const int ny = dims->ny, nz = dims->nz;
     if (nchunks < 1) nchunks = 1;
-    if (nchunks > ny) nchunks = ny;
+    if (nchunks > nz) nchunks = nz;
     cudaStream_t sh = static_cast<cudaStream_t>(stream_h2d);
     cudaStream_t sc = static_cast<cudaStream_t>(stream_compute);
     cudaStream_t sd = static_cast<cudaStream_t>(stream_d2h);
     const size_t row = (size_t)dims->sy * es, plane = (size_t)dims->sz * es;
-    // row range [r0, r1] of chunk q (interior rows 1..ny; the first chunk also
-    // carries halo row 0, the last halo row ny+1)
-    auto rows_of = [&](int q, int* r0, int* r1) {
-        *r0 = 1 + (int)((long long)ny * q / nchunks);
-        *r1 = (int)((long long)ny * (q + 1) / nchunks);
+    const size_t extent = (size_t)field_extent_bytes(*dims, es);
+    // levels [k0, k1) of chunk q
+    auto levels_of = [&](int q, int* k0, int* k1) {
+        *k0 = (int)((long long)nz * q / nchunks);
+        *k1 = (int)((long long)nz * (q + 1) / nchunks);
     };
     std::vector<cudaEvent_t> h2d(nchunks), done(nchunks);
     cudaError_t e = cudaSuccess;
@@ -575,37 +591,33 @@ extern "C" int pw_advect_host_chunked(pw_dtype dtype, const void* u_h, const voi
     void* in_d[3] = {u_d, v_d, w_d};
     void* out_h[3] = {su_h, sv_h, sw_h};
     const void* out_d[3] = {su_d, sv_d, sw_d};
-    // transfers of chunk q's input rows
+    // inputs of chunk q: its whole level planes, one contiguous copy per field
+    // (the last chunk ends at the field's extent)
     for (int q = 0; q < nchunks && e == cudaSuccess; ++q) {
-        int r0, r1;
-        rows_of(q, &r0, &r1);
-        const int a = (q == 0) ? 0 : r0, b = (q == nchunks - 1) ? ny + 1 : r1;
+        int k0, k1;
+        levels_of(q, &k0, &k1);
+        const size_t b0 = (size_t)k0 * plane, b1 = (q == nchunks - 1) ? extent : (size_t)k1 * plane;
         for (int f = 0; f < 3 && e == cudaSuccess; ++f)
-            e = cudaMemcpy2DAsync(static_cast<char*>(in_d[f]) + a * row, plane,
-                                  static_cast<const char*>(in_h[f]) + a * row, plane, (size_t)(b - a + 1) * row, nz,
-                                  cudaMemcpyHostToDevice, sh);
+            e = cudaMemcpyAsync(static_cast<char*>(in_d[f]) + b0, static_cast<const char*>(in_h[f]) + b0, b1 - b0,
+                                cudaMemcpyHostToDevice, sh);
         if (e == cudaSuccess) e = cudaEventRecord(h2d[q], sh);
     }
-    // compute chunk q once chunk q+1 (its upper neighbour rows) has landed
+    // compute chunk q's levels once chunk q+1 (holding level k1, their upper
+    // neighbour) has landed; then its output rows 1..ny of each level go back
     for (int q = 0; q < nchunks && e == cudaSuccess; ++q) {
-        int r0, r1;
-        rows_of(q, &r0, &r1);
+        int k0, k1;
+        levels_of(q, &k0, &k1);
         e = cudaStreamWaitEvent(sc, h2d[q + 1 < nchunks ? q + 1 : q], 0);
         if (e != cudaSuccess) break;
-        pw_dims sub = *dims;
-        sub.ny = r1 - r0 + 1;
-        const size_t off = (size_t)(r0 - 1) * row;
-        rc = pw_advect(dtype, static_cast<const char*>(u_d) + off, static_cast<const char*>(v_d) + off,
-                       static_cast<const char*>(w_d) + off, c, &sub, split, static_cast<char*>(su_d) + off,
-                       static_cast<char*>(sv_d) + off, static_cast<char*>(sw_d) + off, sc);
+        rc = advect_levels(dtype, u_d, v_d, w_d, c, dims, split, su_d, sv_d, sw_d, sc, k0, k1, who);
         if (rc != PW_OK) break;
         e = cudaEventRecord(done[q], sc);
         if (e != cudaSuccess) break;
         e = cudaStreamWaitEvent(sd, done[q], 0);
+        const size_t off = (size_t)k0 * plane + row;
         for (int f = 0; f < 3 && e == cudaSuccess; ++f)
-            e = cudaMemcpy2DAsync(static_cast<char*>(out_h[f]) + r0 * row, plane,
-                                  static_cast<const char*>(out_d[f]) + r0 * row, plane, (size_t)(r1 - r0 + 1) * row,
-                                  nz, cudaMemcpyDeviceToHost, sd);
+            e = cudaMemcpy2DAsync(static_cast<char*>(out_h[f]) + off, plane, static_cast<const char*>(out_d[f]) + off,
+                                  plane, (size_t)ny * row, (size_t)(k1 - k0), cudaMemcpyDeviceToHost, sd);
     }
     for (int q = 0; q < nchunks; ++q) {
         if (h2d[q]) cudaEventDestroy(h2d[q]);

@@ -11,6 +11,7 @@ namespace pw {
 
 struct FwdArgs {
     int nx, ny, nz;
+    int kbeg, kend;            // levels kbeg..kend-1 are computed (0 <= kbeg < kend <= nz)
     long long sy, sz;          // element strides of every field
     int xoff;                  // elements from the descriptors' 16-byte base to i = 0
     int vec;                   // 1: every field's interior i = 1 starts on 16 bytes

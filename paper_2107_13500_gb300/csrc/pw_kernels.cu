@@ -22,6 +22,9 @@ namespace pw {
 constexpr int kF64TX = 32, kF64TY = 8, kF64S = 4;
 using F64Shape = RingShape<double, kF64TX, kF64TY, kF64S>;
 
+// One CTA: a 32x8 tile of columns, output levels kb..ke-1 of its k-chunk
+// (blockIdx.z splits kbeg..kend-1); it reads levels lo = max(kb-1, 0) ..
+// hi = min(ke, nz-1). Loads are numbered relative to lo.
 template <typename Shape>
 __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constant__ CUtensorMap mu,
                                                             const __grid_constant__ CUtensorMap mv,
@@ -38,6 +41,10 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
     const int i = x0 + 1 + tx, j = y0 + 1 + ty;
     const bool act = (i <= a.nx) && (j <= a.ny);
     const int nz = a.nz;
+    const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
+    const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
+    const int lo = kb > 0 ? kb - 1 : 0, hi = ke < nz ? ke : nz - 1;
+    const int nl = hi - lo + 1;  // levels read
 
     if (tid == 0) {
         prefetch_tensormap(&mu);
@@ -46,22 +53,22 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
         ring.init_barriers();
     }
     __syncthreads();
-    int issued = 0;  // meaningful in thread 0 only
+    int issued = 0;  // relative loads issued (thread 0)
     if (tid == 0) {
-        for (; issued < S && issued < nz; ++issued) ring.issue(issued, issued, &mu, &mv, &mw, x0, y0);
+        for (; issued < S && issued < nl; ++issued) ring.issue(issued, lo + issued, &mu, &mv, &mw, x0, y0);
     }
 
     const int c0 = (ty + 1) * BX + (tx + 1) + a.xoff;
     double* __restrict__ su = static_cast<double*>(a.su);
     double* __restrict__ sv = static_cast<double*>(a.sv);
     double* __restrict__ sw = static_cast<double*>(a.sw);
-    size_t g = (size_t)j * (size_t)a.sy + (size_t)i;
     const size_t gsz = (size_t)a.sz;
+    size_t g = (size_t)j * (size_t)a.sy + (size_t)i + (size_t)lo * gsz;
 
     bool bad = !ring.wait(0);
-    if (nz > 1) bad |= !ring.wait(1);
+    if (nl > 1) bad |= !ring.wait(1);
 
-    // Level 1 of the paper (k = 0 here) is not computed; its values feed k = 1.
+    // level-lo values feed the first computed level
     double uo_m, vo_m, wo_m, wx_m, wy_m;
     {
         const double* U = ring.template box<double>(0, 0);
@@ -73,26 +80,27 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
         wx_m = W[c0] + W[c0 + 1];
         wy_m = W[c0] + W[c0 + BX];
     }
-    if (act) {
+    if (act && kb == 0) {  // level 1 of the paper is not computed
         su[g] = 0.0;
         sv[g] = 0.0;
         sw[g] = 0.0;
     }
     bool abort = __syncthreads_or(bad);
-    if (!abort && tid == 0 && issued < nz) {
+    if (!abort && tid == 0 && issued < nl) {
         fence_proxy_async_smem();
-        ring.issue(issued, issued, &mu, &mv, &mw, x0, y0);
+        ring.issue(issued, lo + issued, &mu, &mv, &mw, x0, y0);
         ++issued;
     }
 
     const double tcx = a.tcx, tcy = a.tcy;
-    for (int k = 1; k < nz && !abort; ++k) {
+    for (int k = (kb > 1 ? kb : 1); k < ke && !abort; ++k) {
+        const int r = k - lo;
         g += gsz;
         const bool top = (k == nz - 1);
-        if (!top) bad |= !ring.wait(k + 1);
-        const double* U = ring.template box<double>(k, 0);
-        const double* V = ring.template box<double>(k, 1);
-        const double* W = ring.template box<double>(k, 2);
+        if (!top) bad |= !ring.wait(r + 1);
+        const double* U = ring.template box<double>(r, 0);
+        const double* V = ring.template box<double>(r, 1);
+        const double* W = ring.template box<double>(r, 2);
 
         const double uc = U[c0], uw = U[c0 - 1], ue = U[c0 + 1], us = U[c0 - BX], un = U[c0 + BX];
         const double unw = U[c0 + BX - 1];
@@ -108,9 +116,9 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
         const double wx = wc + we, wy = wc + wn;
         double r_sw = 0.0;
         if (!top) {
-            const double* Uu = ring.template box<double>(k + 1, 0);
-            const double* Vu = ring.template box<double>(k + 1, 1);
-            const double* Wu = ring.template box<double>(k + 1, 2);
+            const double* Uu = ring.template box<double>(r + 1, 0);
+            const double* Vu = ring.template box<double>(r + 1, 1);
+            const double* Wu = ring.template box<double>(r + 1, 2);
             const double uu = Uu[c0], uuw = Uu[c0 - 1];
             const double vu = Vu[c0], vus = Vu[c0 - BX];
             const double wu = Wu[c0];
@@ -131,17 +139,17 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
         wx_m = wx;
         wy_m = wy;
 
-        abort = __syncthreads_or(bad);  // also releases level k's stage
-        if (!abort && tid == 0 && issued < nz) {
+        abort = __syncthreads_or(bad);  // also releases relative level r's stage
+        if (!abort && tid == 0 && issued < nl) {
             fence_proxy_async_smem();
-            ring.issue(issued, issued, &mu, &mv, &mw, x0, y0);
+            ring.issue(issued, lo + issued, &mu, &mv, &mw, x0, y0);
             ++issued;
         }
     }
     if (abort && tid == 0) {
         atomicOr(&tu_status, kStatusTimeout);
         // let every copy still in flight land before the CTA exits
-        for (int lev = (issued > S ? issued - S : 0); lev < issued; ++lev) (void)ring.wait(lev);
+        for (int q = (issued > S ? issued - S : 0); q < issued; ++q) (void)ring.wait(q);
     }
 }
 
@@ -154,7 +162,11 @@ cudaError_t launch_fwd_f64(const CUtensorMap& mu, const CUtensorMap& mv, const C
     auto kern = fwd_f64_kernel<F64Shape>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F64Shape::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.nx + kF64TX - 1) / kF64TX, (a.ny + kF64TY - 1) / kF64TY);
+    const long long tiles = (long long)((a.nx + kF64TX - 1) / kF64TX) * ((a.ny + kF64TY - 1) / kF64TY);
+    int chunks = 1;
+    if ((e = choose_kchunks(kern, F64Shape::NT, F64Shape::SMEM_BYTES, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess)
+        return e;
+    dim3 grid((a.nx + kF64TX - 1) / kF64TX, (a.ny + kF64TY - 1) / kF64TY, chunks);
     kern<<<grid, F64Shape::NT, F64Shape::SMEM_BYTES, st>>>(mu, mv, mw, a);
     return cudaGetLastError();
 }

@@ -307,8 +307,8 @@ __global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_kernel(const __gri
     }
     __syncthreads();
     long long seq = 0;
-    const int kb = (int)((long long)a.nz * blockIdx.z / gridDim.z);
-    const int ke = (int)((long long)a.nz * (blockIdx.z + 1) / gridDim.z);
+    const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
+    const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
     const ConvPlan cp = make_conv_plan(tid);
     (void)paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid, cp);
 }
@@ -363,7 +363,7 @@ cudaError_t launch_fwd_paired(const CUtensorMap& mu, const CUtensorMap& mv, cons
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY);
     int chunks = 1;
-    if ((e = choose_kchunks(fwd_paired_kernel, kNT, kSmemBytes, tiles, a.nz, &chunks)) != cudaSuccess) return e;
+    if ((e = choose_kchunks(fwd_paired_kernel, kNT, kSmemBytes, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess) return e;
     dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY, chunks);
     fwd_paired_kernel<<<grid, kNT, kSmemBytes, st>>>(mu, mv, mw, a);
     return cudaGetLastError();

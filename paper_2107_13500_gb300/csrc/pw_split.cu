@@ -325,8 +325,8 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS) fwd_split_kernel(con
     }
     __syncthreads();
     long long seq = 0;
-    const int kb = (int)((long long)a.nz * blockIdx.z / gridDim.z);
-    const int ke = (int)((long long)a.nz * (blockIdx.z + 1) / gridDim.z);
+    const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
+    const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
     (void)split_tile<Cfg, kVec>(ring, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid);
 }
 
@@ -398,7 +398,7 @@ cudaError_t launch_one(const CUtensorMap& mu, const CUtensorMap& mv, const CUten
     if (e != cudaSuccess) return e;
     const long long tiles = (long long)((a.nx + Cfg::TXP - 1) / Cfg::TXP) * ((a.ny + Cfg::TY - 1) / Cfg::TY);
     int chunks = 1;
-    if ((e = choose_kchunks(kern, Cfg::NT, Cfg::SMEM_BYTES, tiles, a.nz, &chunks)) != cudaSuccess) return e;
+    if ((e = choose_kchunks(kern, Cfg::NT, Cfg::SMEM_BYTES, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess) return e;
     dim3 grid((a.nx + Cfg::TXP - 1) / Cfg::TXP, (a.ny + Cfg::TY - 1) / Cfg::TY, chunks);
     kern<<<grid, Cfg::NT, Cfg::SMEM_BYTES, st>>>(mu, mv, mw, a);
     return cudaGetLastError();

@@ -205,16 +205,16 @@ def test_bounded_wait_gives_up_and_device_stays_usable(gpu, oracle_lib):
     compare_f64(g, o, a, nx, ny)
 
 
-@pytest.mark.parametrize("mode", ["paired", "f32"])
+@pytest.mark.parametrize("mode", ["paired", "f32", "f64"])
 @pytest.mark.parametrize("nchunks", [1, 3, 8, 1000])
 def test_host_chunked_matches_device_call(gpu, mode, nchunks):
-    """pw_advect_host_chunked (y-slab transfers overlapped with compute)
-    gives exactly what pw_advect gives on the same data already on the
-    device; host output halos stay untouched."""
+    """pw_advect_host_chunked (slabs of levels, transfers overlapped with
+    compute) gives exactly what pw_advect gives on the same data already on
+    the device; the host outputs' halo rows stay untouched."""
     import torch
     from paper_2107_13500_gb300 import pw
     nx, ny, nz = 70, 37, 9
-    dt = torch.float64 if mode == "paired" else torch.float32
+    dt = torch.float32 if mode == "f32" else torch.float64
     c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_stretched(nz)).to_device()
     fields = synth.fields_modes(nx, ny, nz, 50.0, 50.0, synth.dz_stretched(nz), seed=21)
     host = [pw.pinned_field(nx, ny, nz, dt) for _ in range(3)]
