@@ -237,8 +237,22 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- our arm
 
+def cpu_model():
+    """The host CPU's model name (lscpu), else the platform's processor string."""
+    try:
+        res = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+        for line in res.stdout.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def cpu_baseline(u, v, w, co, nx, ny, nz):
-    """Oracle on the host cores: repeated full-domain calls for ~10-30 s."""
+    """Oracle on the host cores: repeated full-domain calls for ~10-30 s on
+    all cores, plus one single-thread evaluation."""
     import oracle
     cores = os.cpu_count() or 1
     out = tuple(np.zeros_like(u) for _ in range(3))
@@ -250,8 +264,13 @@ def cpu_baseline(u, v, w, co, nx, ny, nz):
     for _ in range(reps):
         oracle.advect(u, v, w, co, nx, ny, nthreads=cores, out=out)
     dt = (time.perf_counter() - t0) / reps
+    t0 = time.perf_counter()
+    oracle.advect(u, v, w, co, nx, ny, nthreads=1, out=out)
+    dt1 = time.perf_counter() - t0
     return {"value": nx * ny * nz / dt / 1e9, "unit": "GPoints/s", "cores": cores, "kind": "oracle",
-            "sample": f"{reps} full {nx}x{ny}x{nz} evaluations ({reps * dt:.1f} s), OpenMP {cores} threads"}
+            "sample": f"{reps} full {nx}x{ny}x{nz} evaluations ({reps * dt:.1f} s), OpenMP {cores} threads",
+            "single_thread": {"value": nx * ny * nz / dt1 / 1e9, "sample": f"1 full evaluation ({dt1:.1f} s)"},
+            "cpu_model": cpu_model()}
 
 
 def main():
@@ -487,7 +506,55 @@ def extra_modes(torch, pw, oracle, args, sets16, c16, cfg16, ref16, ab16, peak):
     torch.cuda.empty_cache()
     res["batched_96"] = batched_extra(torch, pw)
     res["adjoint_256"] = adjoint_extra(torch, pw)
+    res["c1_64cubed_graph"] = c1_extra(torch, pw, oracle)
     return res
+
+
+def c1_extra(torch, pw, oracle):
+    """64 x 64 x 64 i.i.d. winds, uniform 20 m levels (the correctness
+    configuration; its ~13 MB working set stays in L2), each mode timed as
+    a CUDA graph of 100 launches, with errors against the FP64 oracle."""
+    cfg = synth.config_small_iid()
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    u, v, w = cfg["fields"]()
+    co = oracle.coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"])
+    ref, ab = oracle.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=os.cpu_count() or 1)
+    c = pw.make_coeffs(nz, cfg["dx"], cfg["dy"], cfg["dz"]).to_device()
+    fin = [pw.field_from_numpy(a, nx) for a in (u, v, w)]
+    pts = nx * ny * nz
+    out = {"working_set": "L2-resident (no flush between launches)", "launches_per_graph": 100}
+    for mode in ("f64", "paired", "split"):
+        table = None
+        f = fin
+        if mode == "split":
+            fp, means = zip(*(pw.split_field(t, nx, ny) for t in fin))
+            table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
+            f = list(fp)
+        fout = tuple(pw.field_like(f[0]) for _ in range(3))
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            pw.advect(*f, c, nx, ny, mode=mode, out=fout, split_table=table, stream=s)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(100):
+                    pw.advect(*f, c, nx, ny, mode=mode, out=fout, split_table=table, stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (5 * 100)
+        gout = [t.double().cpu().numpy() for t in fout]
+        out[mode] = {"us_per_launch": ms * 1e3, "GPoints_s": pts / (ms * 1e-3) / 1e9,
+                     "error_vs_oracle": error_stats(gout, ref, ab, nx, ny)}
+        del g
+    return out
 
 
 def batched_extra(torch, pw):

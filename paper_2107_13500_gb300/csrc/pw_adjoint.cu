@@ -13,6 +13,9 @@
 // cells include the halo: gu, gv, gw are defined on every cell the forward
 // map reads. Each thread owns one cell column and marches k with a TMA ring
 // of the six fields (u, v, w, gsu, gsv, gsw) -- no atomics, one write per cell.
+// A launch splits the columns into k-chunks (blockIdx.z) so that small
+// domains still fill the GPU; a chunk of output levels kb..ke-1 reads levels
+// kb-1..ke.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -70,16 +73,16 @@ struct AdjRing {
     }
 };
 
-// Level `lev` (may be -1 or nz: the TMA zero-fills out-of-range levels) goes
-// to stage seq % kS, where seq = lev + 1 counts loads from 0.
+// Load number `seq` of a chunk brings level `lev` (may be -1 or nz: the TMA
+// zero-fills out-of-range levels) into stage seq % kS.
 template <typename T>
-__device__ __forceinline__ void adj_issue(AdjRing<T>& r, const AdjMaps& maps, int seq, int x, int y) {
+__device__ __forceinline__ void adj_issue(AdjRing<T>& r, const AdjMaps& maps, int seq, int lev, int x, int y) {
     using Sh = AdjShape<T>;
     const int s = seq % kS;
     uint64_t* bar = &r.full[s];
     unsigned char* dst = r.base + s * Sh::STAGE_BYTES;
     mbar_arrive_expect_tx(bar, kFields * Sh::BOX_BYTES);
-    for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * Sh::BOX_STRIDE, &maps.m[f], bar, x, y, seq - 1);
+    for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * Sh::BOX_STRIDE, &maps.m[f], bar, x, y, lev);
 }
 
 template <typename T>
@@ -98,7 +101,9 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
     const bool act = (i <= nx + 1) && (j <= ny + 1);
     const int bxs = x0 - Sh::UNIT;  // box x start (tensor coordinate), aligned
     const int bys = y0 - 1;
-    const int nseq = nz + 2;        // levels -1 .. nz
+    const int kb = (int)((long long)nz * blockIdx.z / gridDim.z);
+    const int ke = (int)((long long)nz * (blockIdx.z + 1) / gridDim.z);
+    const int nseq = ke - kb + 2;   // loads: levels kb-1 .. ke
 
     if (tid == 0) {
         for (int f = 0; f < kFields; ++f) prefetch_tensormap(&maps.m[f]);
@@ -108,7 +113,7 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
     __syncthreads();
     int issued = 0;
     if (tid == 0)
-        for (; issued < kS && issued < nseq; ++issued) adj_issue(ring, maps, issued, bxs, bys);
+        for (; issued < kS && issued < nseq; ++issued) adj_issue(ring, maps, issued, kb - 1 + issued, bxs, bys);
 
     // shared index of cell (i, j): tensor x = i + xoff, box starts at bxs
     const int c0 = (ty + 1) * BX + (tx + Sh::UNIT + a.xoff);
@@ -123,16 +128,17 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
     T* __restrict__ gu = static_cast<T*>(a.gu);
     T* __restrict__ gv = static_cast<T*>(a.gv);
     T* __restrict__ gw = static_cast<T*>(a.gw);
-    size_t g = (size_t)j * (size_t)a.sy + (size_t)i;
+    size_t g = (size_t)j * (size_t)a.sy + (size_t)i + (size_t)kb * (size_t)a.sz;
 
     bool bad = false;
-    for (int s = 0; s < 3 && s < nseq; ++s) bad |= !ring.wait(s);  // levels -1, 0, 1
+    for (int s = 0; s < 3 && s < nseq; ++s) bad |= !ring.wait(s);  // levels kb-1, kb, kb+1
     bool abort = __syncthreads_or(bad);
 
-    for (int k = 0; k < nz && !abort; ++k) {
-        if (k > 0) bad |= !ring.wait(k + 2);  // level k+1 (seq k+2)
+    for (int k = kb; k < ke && !abort; ++k) {
+        const int r = k - kb;
+        if (r > 0) bad |= !ring.wait(r + 2);  // level k+1 (load r+2)
         // stages of levels k-1, k, k+1
-        const int sm = (k) % kS, s0 = (k + 1) % kS, sp = (k + 2) % kS;
+        const int sm = r % kS, s0 = (r + 1) % kS, sp = (r + 2) % kS;
         const T* Um = ring.box(sm, 0);
         const T* U0 = ring.box(s0, 0);
         const T* Up = ring.box(sp, 0);
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
         abort = __syncthreads_or(bad);  // level k-1's stage is free
         if (!abort && tid == 0 && issued < nseq) {
             fence_proxy_async_smem();
-            adj_issue(ring, maps, issued, bxs, bys);
+            adj_issue(ring, maps, issued, kb - 1 + issued, bxs, bys);
             ++issued;
         }
     }
@@ -306,18 +312,26 @@ TileShape adjoint_shape(int elem_bytes) {
 cudaError_t launch_adjoint(const CUtensorMap* maps6, int elem_bytes, const AdjArgs& a, cudaStream_t st) {
     AdjMaps m;
     for (int f = 0; f < kFields; ++f) m.m[f] = maps6[f];
-    dim3 grid((a.nx + 2 + kTX - 1) / kTX, (a.ny + 2 + kTY - 1) / kTY);
+    const int tx = (a.nx + 2 + kTX - 1) / kTX, ty = (a.ny + 2 + kTY - 1) / kTY;
+    const long long tiles = (long long)tx * ty;
     cudaError_t e;
+    int chunks = 1;
     if (elem_bytes == 8) {
         e = cudaFuncSetAttribute(adjoint_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  AdjShape<double>::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        adjoint_kernel<double><<<grid, kTX * kTY, AdjShape<double>::SMEM_BYTES, st>>>(m, a);
+        if ((e = choose_kchunks(adjoint_kernel<double>, kTX * kTY, AdjShape<double>::SMEM_BYTES, tiles, a.nz,
+                                &chunks)) != cudaSuccess)
+            return e;
+        adjoint_kernel<double><<<dim3(tx, ty, chunks), kTX * kTY, AdjShape<double>::SMEM_BYTES, st>>>(m, a);
     } else {
         e = cudaFuncSetAttribute(adjoint_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  AdjShape<float>::SMEM_BYTES);
         if (e != cudaSuccess) return e;
-        adjoint_kernel<float><<<grid, kTX * kTY, AdjShape<float>::SMEM_BYTES, st>>>(m, a);
+        if ((e = choose_kchunks(adjoint_kernel<float>, kTX * kTY, AdjShape<float>::SMEM_BYTES, tiles, a.nz,
+                                &chunks)) != cudaSuccess)
+            return e;
+        adjoint_kernel<float><<<dim3(tx, ty, chunks), kTX * kTY, AdjShape<float>::SMEM_BYTES, st>>>(m, a);
     }
     return cudaGetLastError();
 }

@@ -89,12 +89,17 @@ cudaError_t persistent_grid(Kern kern, int threads, int smem, long long n_items,
 
 // Level chunks per tile column so that tiles * chunks work units fill the
 // GPU's resident CTA slots in nearly whole waves. Each chunk re-reads one
-// level below and one above, so chunks stay at least 8 levels tall.
+// level below and one above, so chunks stay at least 8 levels tall -- unless
+// the domain has so few tiles that even 8 chunks each leave most slots idle
+// (a small domain): then up to 64 chunks of at least 2 levels, since a
+// CTA's time is mostly the latency of its serial level march.
 inline int pick_kchunks(long long tiles, int nz, long long slots) {
+    const bool small = tiles * 8 < slots;
+    const int max_chunks = small ? 64 : 8, min_levels = small ? 2 : 8;
     int best = 1;
     double best_cost = 1e300;
-    for (int c = 1; c <= 8; ++c) {
-        if (c > 1 && nz / c < 8) break;
+    for (int c = 1; c <= max_chunks; ++c) {
+        if (c > 1 && nz / c < min_levels) break;
         const double units = (double)tiles * c;
         const double waves = units / (double)slots;
         const double used = waves / (double)((long long)(waves + 0.999999));  // fraction of the last-wave-rounded time
