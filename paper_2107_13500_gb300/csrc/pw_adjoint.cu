@@ -85,11 +85,34 @@ __device__ __forceinline__ void adj_issue(AdjRing<T>& r, const AdjMaps& maps, in
     for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * Sh::BOX_STRIDE, &maps.m[f], bar, x, y, lev);
 }
 
+// The seven vertical coefficients step k uses (zero where the paper's level
+// has no such flux), in T. One thread each loads and converts them once per
+// level; the CTA barrier of the step before publishes them. (A per-thread
+// double->float conversion would run on the FP64 pipe and bound the FP32
+// kernel.)
+template <typename T>
+__device__ __forceinline__ void level_coefs(const AdjArgs& a, int k, int tid, T* dst) {
+    if (tid >= 7) return;
+    const int nz = a.nz;
+    double c = 0.0;
+    switch (tid) {
+        case 0: c = (k + 1 <= nz - 1) ? __ldg(a.tzc1 + k + 1) : 0.0; break;  // tz1p
+        case 1: c = (k >= 1) ? __ldg(a.tzc2 + k - 1) : 0.0; break;           // tz2m
+        case 2: c = __ldg(a.tzc2 + k); break;                                // tz20
+        case 3: c = (k + 1 <= nz - 1) ? __ldg(a.tzd1 + k + 1) : 0.0; break;  // td1p
+        case 4: c = __ldg(a.tzd1 + k); break;                                // td10
+        case 5: c = (k >= 1) ? __ldg(a.tzd2 + k - 1) : 0.0; break;           // td2m
+        default: c = __ldg(a.tzd2 + k); break;                               // td20
+    }
+    dst[tid] = (T)c;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant__ AdjMaps maps, const AdjArgs a) {
     using Sh = AdjShape<T>;
     constexpr int BX = Sh::BX;
     extern __shared__ unsigned char smem_raw[];
+    __shared__ T coef_s[2][8];  // level coefficients, two levels in flight
     AdjRing<T> ring;
     ring.setup(smem_raw);
 
@@ -132,6 +155,7 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
 
     bool bad = false;
     for (int s = 0; s < 3 && s < nseq; ++s) bad |= !ring.wait(s);  // levels kb-1, kb, kb+1
+    level_coefs<T>(a, kb, tid, coef_s[0]);
     bool abort = __syncthreads_or(bad);
 
     for (int k = kb; k < ke && !abort; ++k) {
@@ -165,13 +189,8 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
         const bool w_0 = (k >= 1 && k <= nz - 2);
         const bool w_p = (k + 1 <= nz - 2);
         const bool up0 = (k <= nz - 2);  // level k has an upper flux
-        const T tz1p = (k + 1 <= nz - 1) ? (T)__ldg(a.tzc1 + k + 1) : T(0);
-        const T tz2m = (k >= 1) ? (T)__ldg(a.tzc2 + k - 1) : T(0);
-        const T tz20 = (T)__ldg(a.tzc2 + k);
-        const T td1p = (k + 1 <= nz - 1) ? (T)__ldg(a.tzd1 + k + 1) : T(0);
-        const T td10 = (T)__ldg(a.tzd1 + k);
-        const T td2m = (k >= 1) ? (T)__ldg(a.tzd2 + k - 1) : T(0);
-        const T td20 = (T)__ldg(a.tzd2 + k);
+        const T* cs = coef_s[r & 1];
+        const T tz1p = cs[0], tz2m = cs[1], tz20 = cs[2], td1p = cs[3], td10 = cs[4], td2m = cs[5], td20 = cs[6];
         constexpr int E = 1, N = BX;
 
         // masked cotangents (index: P = C + offset)
@@ -253,6 +272,7 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
             }
         }
         g += (size_t)a.sz;
+        if (k + 1 < ke) level_coefs<T>(a, k + 1, tid, coef_s[(r + 1) & 1]);
         abort = __syncthreads_or(bad);  // level k-1's stage is free
         if (!abort && tid == 0 && issued < nseq) {
             fence_proxy_async_smem();
