@@ -609,15 +609,16 @@ def batched_extra(torch, pw):
 
 def adjoint_extra(torch, pw):
     """256 x 256 x 64 with the small configuration's winds: adjoint kernel
-    time (FP64, FP32) and a 20-step forward-Euler rollout (dt = 0.5 s)
-    differentiated with checkpoints every 5 steps."""
+    time (native FP64, paired FP32, FP32) and a 20-step forward-Euler
+    rollout (dt = 0.5 s) differentiated with checkpoints every 5 steps
+    (native FP64 and paired forward/adjoint)."""
     from paper_2107_13500_gb300 import autograd as pa
     nx, ny, nz = 256, 256, 64
     pts = nx * ny * nz
     u, v, w = synth.fields_iid(nx, ny, nz, seed=1)
     c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0)).to_device()
     out = {"points": pts}
-    for mode, dt in (("f64", torch.float64), ("f32", torch.float32)):
+    for mode, dt in (("f64", torch.float64), ("paired", torch.float64), ("f32", torch.float32)):
         x = [pw.field_from_numpy(a, nx, dt) for a in (u, v, w)]
         g = [pw.field_like(x[0]).uniform_(-1, 1) for _ in range(3)]
         res = tuple(pw.field_like(x[0]) for _ in range(3))
@@ -627,18 +628,19 @@ def adjoint_extra(torch, pw):
     y = [pw.field_like(x0[0]).uniform_(-1, 1) for _ in range(3)]
     inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
 
-    def one():
+    def one(mode):
         xs = [t.clone().requires_grad_() for t in x0]
-        fin = pa.rollout(*xs, c, nx, ny, 0.5, 20, mode="f64", checkpoint_every=5)
+        fin = pa.rollout(*xs, c, nx, ny, 0.5, 20, mode=mode, checkpoint_every=5)
         loss = sum((o[inner] * yy[inner]).sum() for o, yy in zip(fin, y))
         return torch.autograd.grad(loss, xs)
 
-    one()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    one()
-    torch.cuda.synchronize()
-    out["rollout20_ckpt5_f64_s"] = time.perf_counter() - t0
+    for mode in ("f64", "paired"):
+        one(mode)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        one(mode)
+        torch.cuda.synchronize()
+        out[f"rollout20_ckpt5_{mode}_s"] = time.perf_counter() - t0
     return out
 
 

@@ -170,7 +170,9 @@ int pw_split_field(const double *f, const pw_dims *dims_f, float *fp, const pw_d
  * Results cover every cell the forward map reads, halo included
  * (i = 0..nx+1, j = 0..ny+1, all k); accumulate != 0 adds them to gu, gv, gw,
  * otherwise they overwrite. Cells beyond i = nx+1 (row padding) are not
- * touched. dtype PW_F64 (double, native FP64) or PW_F32 (float). All nine
+ * touched. dtype PW_F64 (double, native FP64), PW_F64_PAIRED (double,
+ * paired-FP32 arithmetic as in pw_advect, within 1e-13 of native FP64) or
+ * PW_F32 (float). All nine
  * fields share `dims`; u, v, w, gsu, gsv, gsw must have the same address
  * modulo 16 bytes. Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_EUNSUPPORTED,
  * PW_ECUDA.

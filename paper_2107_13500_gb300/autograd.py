@@ -15,7 +15,7 @@ from torch.utils.checkpoint import checkpoint
 from . import pw
 
 # forward mode -> adjoint arithmetic
-_ADJ_MODE = {"f64": "f64", "paired": "f64", "f32": "f32"}
+_ADJ_MODE = {"f64": "f64", "paired": "paired", "f32": "f32"}
 
 
 def _as_field(t, like):

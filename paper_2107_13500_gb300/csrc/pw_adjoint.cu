@@ -21,6 +21,7 @@
 
 #include "pw_common.cuh"
 #include "pw_internal.h"
+#include "pw_pair.cuh"
 #include "pw_ring.cuh"
 
 namespace pw {
@@ -90,21 +91,22 @@ __device__ __forceinline__ void adj_issue(AdjRing<T>& r, const AdjMaps& maps, in
 // level; the CTA barrier of the step before publishes them. (A per-thread
 // double->float conversion would run on the FP64 pipe and bound the FP32
 // kernel.)
+__device__ __forceinline__ double level_coef(const AdjArgs& a, int k, int n) {
+    const int nz = a.nz;
+    switch (n) {
+        case 0: return (k + 1 <= nz - 1) ? __ldg(a.tzc1 + k + 1) : 0.0;  // tz1p
+        case 1: return (k >= 1) ? __ldg(a.tzc2 + k - 1) : 0.0;           // tz2m
+        case 2: return __ldg(a.tzc2 + k);                                // tz20
+        case 3: return (k + 1 <= nz - 1) ? __ldg(a.tzd1 + k + 1) : 0.0;  // td1p
+        case 4: return __ldg(a.tzd1 + k);                                // td10
+        case 5: return (k >= 1) ? __ldg(a.tzd2 + k - 1) : 0.0;           // td2m
+        default: return __ldg(a.tzd2 + k);                               // td20
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void level_coefs(const AdjArgs& a, int k, int tid, T* dst) {
-    if (tid >= 7) return;
-    const int nz = a.nz;
-    double c = 0.0;
-    switch (tid) {
-        case 0: c = (k + 1 <= nz - 1) ? __ldg(a.tzc1 + k + 1) : 0.0; break;  // tz1p
-        case 1: c = (k >= 1) ? __ldg(a.tzc2 + k - 1) : 0.0; break;           // tz2m
-        case 2: c = __ldg(a.tzc2 + k); break;                                // tz20
-        case 3: c = (k + 1 <= nz - 1) ? __ldg(a.tzd1 + k + 1) : 0.0; break;  // td1p
-        case 4: c = __ldg(a.tzd1 + k); break;                                // td10
-        case 5: c = (k >= 1) ? __ldg(a.tzd2 + k - 1) : 0.0; break;           // td2m
-        default: c = __ldg(a.tzd2 + k); break;                               // td20
-    }
-    dst[tid] = (T)c;
+    if (tid < 7) dst[tid] = (T)level_coef(a, k, tid);
 }
 
 template <typename T>
@@ -286,6 +288,299 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
     }
 }
 
+// ---------------------------------------------------------------------------
+// Paired-FP32 adjoint (PW_F64_PAIRED): doubles in and out, the same gather on
+// (hi, lo) float pairs (pw_pair.cuh). A 2-stage TMA ring brings the six
+// fields of a level as doubles; each level is split once into a three-level
+// pair ring, and a thread evaluates cells A = (x0+t, j) and B = A + 16 on
+// packed lanes, reading every neighbour of both as one 16-byte item of the
+// interleaved halves (as in the paired forward kernel). Level k-1's values
+// the gather needs are carried in registers.
+//
+// Cotangents that the forward map never produces (halo cells, level 1, and
+// the top level of sw) are set to zero while they are split, so the gather
+// needs no per-cell masks; only the upper vertical fluxes of su and sv, absent
+// at the top level, are skipped by a level-uniform test.
+
+constexpr int kPS = 2, kPPL = 3;                    // TMA stages, pair-ring levels
+constexpr int kPHalf = kTX / 2;                    // x distance from A to B; threads per tile row
+constexpr int kPNT = kPHalf * kTY;
+constexpr int kPHX = kPHalf + 2;                   // pair-box row: x' = 0..kPHalf+1 of both halves
+using PSh = AdjShape<double>;
+constexpr int kPItems = PSh::BY * kPHX;            // float4 {hA, hB, lA, lB} per field and level
+constexpr int kPPairOffset = kPS * PSh::STAGE_BYTES + 64;
+constexpr int kPPairBytes = kPPL * kFields * kPItems * 16;
+constexpr int kPCoefOffset = kPPairOffset + kPPairBytes;
+constexpr int kPCoefBytes = kPPL * 8 * 16;
+constexpr int kPSmemBytes = kPCoefOffset + kPCoefBytes + 128;
+constexpr int kPConvIters = (kFields * kPItems + kPNT - 1) / kPNT;
+static_assert(PSh::BOX_STRIDE % 8 == 0, "box stride in doubles");
+// lane A of item x' is box column x' + 1 + xoff (the box starts one 16-byte
+// unit left of the tile), lane B kPHalf further
+static_assert((kPHX - 1) + 1 + PSh::XOFF_MAX + kPHalf < PSh::BX, "both halves must lie inside the box row");
+
+// Per-thread split work: item tid + q*kPNT of a level is (field, row, x');
+// offsets and positions depend on neither the level nor the tile.
+struct AdjConvPlan {
+    int off[kPConvIters];   // lane A's double offset in a stage (xoff = 0)
+    int info[kPConvIters];  // field | row << 8 | x' << 16
+};
+
+__device__ __forceinline__ AdjConvPlan make_adj_conv_plan(int tid) {
+    AdjConvPlan cp;
+#pragma unroll
+    for (int q = 0; q < kPConvIters; ++q) {
+        const int n = tid + q * kPNT;
+        const int f = n / kPItems, e = n - f * kPItems;
+        const int row = e / kPHX, xp = e - row * kPHX;
+        cp.off[q] = f * (PSh::BOX_STRIDE / 8) + row * PSh::BX + xp + 1;
+        cp.info[q] = f | (row << 8) | (xp << 16);
+    }
+    return cp;
+}
+
+// Split the level `lev` held in `stage` into pair slot `dst`; cotangent cells
+// outside the computed output points become (0, 0). Threads 0..6 also store
+// the level's seven coefficients (as for the FP64 kernel) as pairs {h, h, l, l}.
+__device__ __forceinline__ void adj_convert(const unsigned char* stage, float4* dst, float4* cdst, int lev,
+                                            int x0, int y0, const AdjArgs& a, int tid, const AdjConvPlan& cp) {
+    const double* base = reinterpret_cast<const double*>(stage) + a.xoff;
+    const bool s_ok = lev >= 1;                    // su, sv: levels 1..nz-1 (level nz reads as 0)
+    const bool w_ok = lev >= 1 && lev <= a.nz - 2; // sw: levels 1..nz-2
+#pragma unroll
+    for (int q = 0; q < kPConvIters; ++q) {
+        const int n = tid + q * kPNT;
+        if ((q + 1) * kPNT <= kFields * kPItems || n < kFields * kPItems) {
+            const double* src = base + cp.off[q];
+            double da = src[0], db = src[kPHalf];
+            const int f = cp.info[q] & 0xff;
+            if (f >= 3) {
+                const int row = (cp.info[q] >> 8) & 0xff, xp = cp.info[q] >> 16;
+                const int ia = x0 - 1 + xp, j = y0 - 1 + row;
+                const bool lv = (f == 5) ? w_ok : s_ok;
+                const bool jy = lv && j >= 1 && j <= a.ny;
+                da = (jy && ia >= 1 && ia <= a.nx) ? da : 0.0;
+                db = (jy && ia + kPHalf >= 1 && ia + kPHalf <= a.nx) ? db : 0.0;
+            }
+            const pf p0 = split_double(da), p1 = split_double(db);
+            dst[n] = make_float4(p0.h, p1.h, p0.l, p1.l);
+        }
+    }
+    if (tid < 7 && lev >= 0 && lev < a.nz) {
+        const pf p = split_double(level_coef(a, lev, tid));
+        cdst[tid] = make_float4(p.h, p.h, p.l, p.l);
+    }
+}
+
+__device__ __forceinline__ pf2 ldp(const float4* b, int idx) {
+    const float4 v = b[idx];
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+__device__ __forceinline__ pf2 cf2(const float4* c, int n) {
+    const float4 v = c[n];
+    return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
+}
+
+__device__ __forceinline__ void adj_issue_p(unsigned char* base, uint64_t* full, const AdjMaps& maps, int seq, int lev,
+                                            int x, int y) {
+    const int s = seq % kPS;
+    uint64_t* bar = &full[s];
+    unsigned char* dst = base + s * PSh::STAGE_BYTES;
+    mbar_arrive_expect_tx(bar, kFields * PSh::BOX_BYTES);
+    for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * PSh::BOX_STRIDE, &maps.m[f], bar, x, y, lev);
+}
+
+__global__ void __launch_bounds__(kPNT, 1) adjoint_paired_kernel(const __grid_constant__ AdjMaps maps,
+                                                                 const AdjArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + kPS * PSh::STAGE_BYTES);
+    float4* pairs = reinterpret_cast<float4*>(base + kPPairOffset);
+    float4* coefs = reinterpret_cast<float4*>(base + kPCoefOffset);
+    auto slot = [&](int rel) { return pairs + (rel % kPPL) * kFields * kPItems; };
+    auto cslot = [&](int rel) { return coefs + (rel % kPPL) * 8; };
+    auto wait = [&](int seq) { return mbar_wait_bounded(&full[seq % kPS], (uint32_t)((seq / kPS) & 1)); };
+
+    const int tid = threadIdx.x;
+    const int tx = tid % kPHalf, ty = tid / kPHalf;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int ia = x0 + tx, j = y0 + ty;  // cell A; B is ia + kPHalf
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool act_a = (ia <= nx + 1) && (j <= ny + 1);
+    const bool act_b = (ia + kPHalf <= nx + 1) && (j <= ny + 1);
+    const int bxs = x0 - PSh::UNIT, bys = y0 - 1;
+    const int kb = (int)((long long)nz * blockIdx.z / gridDim.z);
+    const int ke = (int)((long long)nz * (blockIdx.z + 1) / gridDim.z);
+    const int nl = ke - kb + 2;  // loads: levels kb-1 .. ke (relative 0 .. nl-1)
+    const AdjConvPlan cp = make_adj_conv_plan(tid);
+
+    if (tid == 0) {
+        for (int f = 0; f < kFields; ++f) prefetch_tensormap(&maps.m[f]);
+        for (int s = 0; s < kPS; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    int issued = 0;
+    if (tid == 0)
+        for (; issued < kPS && issued < nl; ++issued) adj_issue_p(base, full, maps, issued, kb - 1 + issued, bxs, bys);
+
+    // relative levels 0..2 split up front, each stage reissued once split
+    bool bad = false, abort = false;
+    for (int r = 0; r < kPPL && r < nl && !abort; ++r) {
+        bad |= !wait(r);
+        adj_convert(base + (r % kPS) * PSh::STAGE_BYTES, slot(r), cslot(r), kb - 1 + r, x0, y0, a, tid, cp);
+        abort = __syncthreads_or(bad);
+        if (!abort && tid == 0 && issued < nl) {
+            fence_proxy_async_smem();
+            adj_issue_p(base, full, maps, issued, kb - 1 + issued, bxs, bys);
+            ++issued;
+        }
+    }
+
+    const int c = (ty + 1) * kPHX + (tx + 1);
+    constexpr int E = 1, N = kPHX;
+    const pf2 tcx = dup2(split_double(a.tcx)), tcy = dup2(split_double(a.tcy));
+    // level k-1 carries: w at C, C+x, C+y; su, sv at C; sw at C, C+x, C+y
+    pf2 w_kmc, w_kme, w_kmn, su_km, sv_km, sw_km, sw_km_e, sw_km_n;
+    {
+        const float4* L = slot(0);
+        w_kmc = ldp(L + 2 * kPItems, c);
+        w_kme = ldp(L + 2 * kPItems, c + E);
+        w_kmn = ldp(L + 2 * kPItems, c + N);
+        su_km = ldp(L + 3 * kPItems, c);
+        sv_km = ldp(L + 4 * kPItems, c);
+        sw_km = ldp(L + 5 * kPItems, c);
+        sw_km_e = ldp(L + 5 * kPItems, c + E);
+        sw_km_n = ldp(L + 5 * kPItems, c + N);
+    }
+    double* __restrict__ gu = static_cast<double*>(a.gu);
+    double* __restrict__ gv = static_cast<double*>(a.gv);
+    double* __restrict__ gw = static_cast<double*>(a.gw);
+    size_t g = (size_t)j * (size_t)a.sy + (size_t)ia + (size_t)kb * (size_t)a.sz;
+    abort = __syncthreads_or(bad);  // relative slot 0 is rewritten by the first step
+
+    for (int k = kb; k < ke && !abort; ++k) {
+        const int rc = k - kb + 1;  // relative level of k
+        if (rc + 2 < nl) {
+            bad |= !wait(rc + 2);
+            adj_convert(base + ((rc + 2) % kPS) * PSh::STAGE_BYTES, slot(rc + 2), cslot(rc + 2), k + 2, x0, y0, a,
+                        tid, cp);
+        }
+        const float4* L0 = slot(rc);
+        const float4* Lp = slot(rc + 1);
+        const float4* U0 = L0;
+        const float4* V0 = L0 + kPItems;
+        const float4* W0 = L0 + 2 * kPItems;
+        const float4* GU0 = L0 + 3 * kPItems;
+        const float4* GV0 = L0 + 4 * kPItems;
+        const float4* GW0 = L0 + 5 * kPItems;
+        const float4* Up = Lp;
+        const float4* Vp = Lp + kPItems;
+        const float4* Wp = Lp + 2 * kPItems;
+        const float4* GUp = Lp + 3 * kPItems;
+        const float4* GVp = Lp + 4 * kPItems;
+        const float4* GWp = Lp + 5 * kPItems;
+        const float4* C0 = cslot(rc);
+        const bool up0 = (k <= nz - 2);  // level k has an upper flux
+
+        const pf2 su_c = ldp(GU0, c), su_e = ldp(GU0, c + E), su_w = ldp(GU0, c - E), su_n = ldp(GU0, c + N);
+        const pf2 su_s = ldp(GU0, c - N), su_nw = ldp(GU0, c + N - E);
+        const pf2 su_kp = ldp(GUp, c), su_kp_w = ldp(GUp, c - E);
+        const pf2 sv_c = ldp(GV0, c), sv_e = ldp(GV0, c + E), sv_w = ldp(GV0, c - E), sv_n = ldp(GV0, c + N);
+        const pf2 sv_s = ldp(GV0, c - N), sv_se = ldp(GV0, c - N + E);
+        const pf2 sv_kp = ldp(GVp, c), sv_kp_s = ldp(GVp, c - N);
+        const pf2 sw_c = ldp(GW0, c), sw_e = ldp(GW0, c + E), sw_w = ldp(GW0, c - E), sw_n = ldp(GW0, c + N);
+        const pf2 sw_s = ldp(GW0, c - N), sw_kp = ldp(GWp, c);
+        const pf2 u_c = ldp(U0, c), u_e = ldp(U0, c + E), u_w = ldp(U0, c - E), u_n = ldp(U0, c + N);
+        const pf2 u_nw = ldp(U0, c + N - E), u_kp = ldp(Up, c), u_kp_w = ldp(Up, c - E);
+        const pf2 v_c = ldp(V0, c), v_e = ldp(V0, c + E), v_n = ldp(V0, c + N), v_s = ldp(V0, c - N);
+        const pf2 v_se = ldp(V0, c - N + E), v_kp = ldp(Vp, c), v_kp_s = ldp(Vp, c - N);
+        const pf2 w_c = ldp(W0, c), w_e = ldp(W0, c + E), w_n = ldp(W0, c + N), w_kp = ldp(Wp, c);
+        const pf2 tz1p = cf2(C0, 0), tz2m = cf2(C0, 1), tz20 = cf2(C0, 2), td1p = cf2(C0, 3), td10 = cf2(C0, 4);
+        const pf2 td2m = cf2(C0, 5), td20 = cf2(C0, 6);
+
+        // gu(C) (same terms and order as the FP64 kernel)
+        pf2 r_u = pmul2(tcx, psub2(psub2(padd2(pmul2(padd2(padd2(u_e, u_c), u_c), su_e), pmul2(u_w, su_c)),
+                                         pmul2(padd2(padd2(u_w, u_c), u_c), su_w)),
+                                   pmul2(u_e, su_c)));
+        r_u = padd2(r_u, pmul2(tcy, psub2(pmul2(padd2(v_c, v_e), su_n), pmul2(padd2(v_s, v_se), su_s))));
+        r_u = padd2(r_u, psub2(pmul2(pmul2(tz1p, padd2(w_c, w_e)), su_kp), pmul2(pmul2(tz2m, padd2(w_kmc, w_kme)), su_km)));
+        r_u = padd2(r_u, pmul2(tcx, psub2(psub2(padd2(pmul2(v_c, sv_e), pmul2(v_s, sv_se)), pmul2(v_e, sv_c)),
+                                         pmul2(v_se, sv_s))));
+        r_u = padd2(r_u, pmul2(tcx, psub2(psub2(padd2(pmul2(w_c, sw_e), pmul2(w_kmc, sw_km_e)), pmul2(w_e, sw_c)),
+                                         pmul2(w_kme, sw_km))));
+        // gv(C)
+        pf2 r_v = pmul2(tcy, psub2(psub2(padd2(pmul2(padd2(padd2(v_n, v_c), v_c), sv_n), pmul2(v_s, sv_c)),
+                                         pmul2(padd2(padd2(v_s, v_c), v_c), sv_s)),
+                                   pmul2(v_n, sv_c)));
+        r_v = padd2(r_v, pmul2(tcx, psub2(pmul2(padd2(u_c, u_n), sv_e), pmul2(padd2(u_w, u_nw), sv_w))));
+        r_v = padd2(r_v, psub2(pmul2(pmul2(tz1p, padd2(w_c, w_n)), sv_kp), pmul2(pmul2(tz2m, padd2(w_kmc, w_kmn)), sv_km)));
+        r_v = padd2(r_v, pmul2(tcy, psub2(psub2(padd2(pmul2(u_c, su_n), pmul2(u_w, su_nw)), pmul2(u_n, su_c)),
+                                         pmul2(u_nw, su_w))));
+        r_v = padd2(r_v, pmul2(tcy, psub2(psub2(padd2(pmul2(w_c, sw_n), pmul2(w_kmc, sw_km_n)), pmul2(w_n, sw_c)),
+                                         pmul2(w_kmn, sw_km))));
+        // gw(C)
+        pf2 r_w = pmul2(tz1p, padd2(pmul2(u_c, su_kp), pmul2(u_w, su_kp_w)));
+        pf2 r_w2 = pmul2(tz1p, padd2(pmul2(v_c, sv_kp), pmul2(v_s, sv_kp_s)));
+        if (up0) {  // the upper fluxes of su and sv at level k
+            r_w = psub2(r_w, pmul2(tz20, padd2(pmul2(u_kp, su_c), pmul2(u_kp_w, su_w))));
+            r_w2 = psub2(r_w2, pmul2(tz20, padd2(pmul2(v_kp, sv_c), pmul2(v_kp_s, sv_s))));
+        }
+        r_w = padd2(r_w, r_w2);
+        r_w = padd2(r_w, pmul2(tcx, psub2(pmul2(padd2(u_c, u_kp), sw_e), pmul2(padd2(u_w, u_kp_w), sw_w))));
+        r_w = padd2(r_w, pmul2(tcy, psub2(pmul2(padd2(v_c, v_kp), sw_n), pmul2(padd2(v_s, v_kp_s), sw_s))));
+        r_w = padd2(r_w, padd2(pmul2(pmul2(td1p, padd2(padd2(w_kp, w_c), w_c)), sw_kp), pmul2(pmul2(td10, w_kmc), sw_c)));
+        r_w = psub2(r_w, padd2(pmul2(pmul2(td2m, padd2(padd2(w_kmc, w_c), w_c)), sw_km), pmul2(pmul2(td20, w_kp), sw_c)));
+
+        const double ua = pair_to_double(pf{r_u.h.x, r_u.l.x}), ub = pair_to_double(pf{r_u.h.y, r_u.l.y});
+        const double va = pair_to_double(pf{r_v.h.x, r_v.l.x}), vb = pair_to_double(pf{r_v.h.y, r_v.l.y});
+        const double wa = pair_to_double(pf{r_w.h.x, r_w.l.x}), wb = pair_to_double(pf{r_w.h.y, r_w.l.y});
+        if (a.accumulate) {
+            if (act_a) {
+                gu[g] += ua;
+                gv[g] += va;
+                gw[g] += wa;
+            }
+            if (act_b) {
+                gu[g + kPHalf] += ub;
+                gv[g + kPHalf] += vb;
+                gw[g + kPHalf] += wb;
+            }
+        } else {
+            if (act_a) {
+                gu[g] = ua;
+                gv[g] = va;
+                gw[g] = wa;
+            }
+            if (act_b) {
+                gu[g + kPHalf] = ub;
+                gv[g + kPHalf] = vb;
+                gw[g + kPHalf] = wb;
+            }
+        }
+        g += (size_t)a.sz;
+        w_kmc = w_c;
+        w_kme = w_e;
+        w_kmn = w_n;
+        su_km = su_c;
+        sv_km = sv_c;
+        sw_km = sw_c;
+        sw_km_e = sw_e;
+        sw_km_n = sw_n;
+        abort = __syncthreads_or(bad);  // publishes rc+2's pairs, frees rc's slot and rc+2's stage
+        if (!abort && tid == 0 && issued < nl) {
+            fence_proxy_async_smem();
+            adj_issue_p(base, full, maps, issued, kb - 1 + issued, bxs, bys);
+            ++issued;
+        }
+    }
+    if (abort && tid == 0) {
+        atomicOr(&tu_status, kStatusTimeout);
+        for (int q = (issued > kPS ? issued - kPS : 0); q < issued; ++q) (void)wait(q);
+    }
+}
+
 // Transpose of the periodic halo fill: halo rows are added into the rows
 // they were copied from and cleared, then halo columns likewise (the fill
 // copied columns first, then full rows).
@@ -353,6 +648,20 @@ cudaError_t launch_adjoint(const CUtensorMap* maps6, int elem_bytes, const AdjAr
             return e;
         adjoint_kernel<float><<<dim3(tx, ty, chunks), kTX * kTY, AdjShape<float>::SMEM_BYTES, st>>>(m, a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_paired(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st) {
+    AdjMaps m;
+    for (int f = 0; f < kFields; ++f) m.m[f] = maps6[f];
+    const int tx = (a.nx + 2 + kTX - 1) / kTX, ty = (a.ny + 2 + kTY - 1) / kTY;
+    cudaError_t e = cudaFuncSetAttribute(adjoint_paired_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmemBytes);
+    if (e != cudaSuccess) return e;
+    int chunks = 1;
+    if ((e = choose_kchunks(adjoint_paired_kernel, kPNT, kPSmemBytes, (long long)tx * ty, a.nz, &chunks)) !=
+        cudaSuccess)
+        return e;
+    adjoint_paired_kernel<<<dim3(tx, ty, chunks), kPNT, kPSmemBytes, st>>>(m, a);
     return cudaGetLastError();
 }
 

@@ -372,8 +372,9 @@ extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, c
                                  const pw_dims* dims, const void* gsu, const void* gsv, const void* gsw, void* gu,
                                  void* gv, void* gw, int accumulate, void* stream) {
     const char* who = "pw_advect_adjoint";
-    if (dtype != PW_F64 && dtype != PW_F32)
-        return fail(known_dtype(dtype) ? PW_EUNSUPPORTED : PW_EINVAL, "%s: dtype must be PW_F64 or PW_F32", who);
+    if (dtype != PW_F64 && dtype != PW_F32 && dtype != PW_F64_PAIRED)
+        return fail(known_dtype(dtype) ? PW_EUNSUPPORTED : PW_EINVAL,
+                    "%s: dtype must be PW_F64, PW_F64_PAIRED or PW_F32", who);
     const int es = elem_size(dtype);
     int rc = check_dims(dims, es, who);
     if (rc) return rc;
@@ -414,7 +415,8 @@ extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, c
     a.gv = gv;
     a.gw = gw;
     a.accumulate = accumulate ? 1 : 0;
-    cudaError_t e = pw::launch_adjoint(maps, es, a, static_cast<cudaStream_t>(stream));
+    cudaError_t e = dtype == PW_F64_PAIRED ? pw::launch_adjoint_paired(maps, a, static_cast<cudaStream_t>(stream))
+                                           : pw::launch_adjoint(maps, es, a, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;
 }

@@ -151,6 +151,8 @@ struct AdjArgs {
 TileShape adjoint_shape(int elem_bytes);
 // maps6: u, v, w, gsu, gsv, gsw
 cudaError_t launch_adjoint(const CUtensorMap* maps6, int elem_bytes, const AdjArgs& a, cudaStream_t st);
+// PW_F64_PAIRED: double fields, the box of adjoint_shape(8)
+cudaError_t launch_adjoint_paired(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st);
 cudaError_t launch_fold_halo(void* field, int elem_bytes, int nx, int ny, int nz, long long sy, long long sz,
                              cudaStream_t st);
 

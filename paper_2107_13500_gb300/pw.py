@@ -384,10 +384,11 @@ def device_status(stream=None) -> int:
 def advect_adjoint(u, v, w, coeffs: Coefficients, nx, ny, gsu, gsv, gsw, mode="f64", out=None, accumulate=False,
                    stream=None):
     """(gu, gv, gw) = J(u, v, w)^T (gsu, gsv, gsw) on every cell the forward
-    reads (halo included). mode "f64" (double) or "f32" (float). Cotangents
-    must share u's layout (shape, strides, 16-byte phase)."""
+    reads (halo included). mode "f64" (double, native FP64), "paired"
+    (double, paired-FP32 arithmetic) or "f32" (float). Cotangents must share
+    u's layout (shape, strides, 16-byte phase)."""
     lib = load_library()
-    dt = {"f64": PW_F64, "f32": PW_F32}[mode]
+    dt = {"f64": PW_F64, "paired": PW_F64_PAIRED, "f32": PW_F32}[mode]
     d = dims_of(u, nx, ny)
     ins = (u, v, w, gsu, gsv, gsw)
     for t in ins[1:]:
