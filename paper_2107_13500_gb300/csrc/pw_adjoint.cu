@@ -290,8 +290,9 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
 
 // ---------------------------------------------------------------------------
 // Paired-FP32 adjoint (PW_F64_PAIRED): doubles in and out, the same gather on
-// (hi, lo) float pairs (pw_pair.cuh). A 2-stage TMA ring brings the six
-// fields of a level as doubles; each level is split once into a three-level
+// (hi, lo) float pairs (pw_pair.cuh). A one-level TMA stage brings the six
+// fields of a level as doubles (reissued as soon as the level is split, a
+// full step ahead of its use; one stage keeps three CTAs per SM); each level is split once into a three-level
 // pair ring, and a thread evaluates cells A = (x0+t, j) and B = A + 16 on
 // packed lanes, reading every neighbour of both as one 16-byte item of the
 // interleaved halves (as in the paired forward kernel). Level k-1's values
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
 // needs no per-cell masks; only the upper vertical fluxes of su and sv, absent
 // at the top level, are skipped by a level-uniform test.
 
-constexpr int kPS = 2, kPPL = 3;                    // TMA stages, pair-ring levels
+constexpr int kPS = 1, kPPL = 3;                    // TMA stages, pair-ring levels
 constexpr int kPHalf = kTX / 2;                    // x distance from A to B; threads per tile row
 constexpr int kPNT = kPHalf * kTY;
 constexpr int kPHX = kPHalf + 2;                   // pair-box row: x' = 0..kPHalf+1 of both halves
