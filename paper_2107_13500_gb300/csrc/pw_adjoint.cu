@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
 
     for (int k = kb; k < ke && !abort; ++k) {
         const int r = k - kb;
+        // next level's coefficient, loaded now so that its latency is hidden by the step
+        const double c_next = (tid < 7 && k + 1 < ke) ? level_coef(a, k + 1, tid) : 0.0;
         if (r > 0) bad |= !ring.wait(r + 2);  // level k+1 (load r+2)
         // stages of levels k-1, k, k+1
         const int sm = r % kS, s0 = (r + 1) % kS, sp = (r + 2) % kS;
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
             }
         }
         g += (size_t)a.sz;
-        if (k + 1 < ke) level_coefs<T>(a, k + 1, tid, coef_s[(r + 1) & 1]);
+        if (tid < 7 && k + 1 < ke) coef_s[(r + 1) & 1][tid] = (T)c_next;
         abort = __syncthreads_or(bad);  // level k-1's stage is free
         if (!abort && tid == 0 && issued < nseq) {
             fence_proxy_async_smem();
@@ -340,11 +342,19 @@ __device__ __forceinline__ AdjConvPlan make_adj_conv_plan(int tid) {
     return cp;
 }
 
+// Coefficient n = tid of level lev for threads 0..6 (0 elsewhere and for
+// levels outside the domain).
+__device__ __forceinline__ double adj_coef_for(const AdjArgs& a, int lev, int tid) {
+    return (tid < 7 && lev >= 0 && lev < a.nz) ? level_coef(a, lev, tid) : 0.0;
+}
+
 // Split the level `lev` held in `stage` into pair slot `dst`; cotangent cells
 // outside the computed output points become (0, 0). Threads 0..6 also store
-// the level's seven coefficients (as for the FP64 kernel) as pairs {h, h, l, l}.
+// the level's seven coefficients (as for the FP64 kernel), given in `coef`
+// (loaded one conversion earlier), as pairs {h, h, l, l}.
 __device__ __forceinline__ void adj_convert(const unsigned char* stage, float4* dst, float4* cdst, int lev,
-                                            int x0, int y0, const AdjArgs& a, int tid, const AdjConvPlan& cp) {
+                                            int x0, int y0, const AdjArgs& a, int tid, const AdjConvPlan& cp,
+                                            double coef) {
     const double* base = reinterpret_cast<const double*>(stage) + a.xoff;
     const bool s_ok = lev >= 1;                    // su, sv: levels 1..nz-1 (level nz reads as 0)
     const bool w_ok = lev >= 1 && lev <= a.nz - 2; // sw: levels 1..nz-2
@@ -368,7 +378,7 @@ __device__ __forceinline__ void adj_convert(const unsigned char* stage, float4* 
         }
     }
     if (tid < 7 && lev >= 0 && lev < a.nz) {
-        const pf p = split_double(level_coef(a, lev, tid));
+        const pf p = split_double(coef);
         cdst[tid] = make_float4(p.h, p.h, p.l, p.l);
     }
 }
@@ -392,7 +402,7 @@ __device__ __forceinline__ void adj_issue_p(unsigned char* base, uint64_t* full,
     for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * PSh::BOX_STRIDE, &maps.m[f], bar, x, y, lev);
 }
 
-__global__ void __launch_bounds__(kPNT, 1) adjoint_paired_kernel(const __grid_constant__ AdjMaps maps,
+__global__ void __launch_bounds__(kPNT, 3) adjoint_paired_kernel(const __grid_constant__ AdjMaps maps,
                                                                  const AdjArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -426,11 +436,14 @@ __global__ void __launch_bounds__(kPNT, 1) adjoint_paired_kernel(const __grid_co
     if (tid == 0)
         for (; issued < kPS && issued < nl; ++issued) adj_issue_p(base, full, maps, issued, kb - 1 + issued, bxs, bys);
 
-    // relative levels 0..2 split up front, each stage reissued once split
+    // relative levels 0..2 split up front, each stage reissued once split;
+    // c_pre is the next level's coefficient, loaded one conversion ahead
     bool bad = false, abort = false;
+    double c_pre = adj_coef_for(a, kb - 1, tid);
     for (int r = 0; r < kPPL && r < nl && !abort; ++r) {
         bad |= !wait(r);
-        adj_convert(base + (r % kPS) * PSh::STAGE_BYTES, slot(r), cslot(r), kb - 1 + r, x0, y0, a, tid, cp);
+        adj_convert(base + (r % kPS) * PSh::STAGE_BYTES, slot(r), cslot(r), kb - 1 + r, x0, y0, a, tid, cp, c_pre);
+        c_pre = adj_coef_for(a, kb + r, tid);
         abort = __syncthreads_or(bad);
         if (!abort && tid == 0 && issued < nl) {
             fence_proxy_async_smem();
@@ -466,7 +479,8 @@ __global__ void __launch_bounds__(kPNT, 1) adjoint_paired_kernel(const __grid_co
         if (rc + 2 < nl) {
             bad |= !wait(rc + 2);
             adj_convert(base + ((rc + 2) % kPS) * PSh::STAGE_BYTES, slot(rc + 2), cslot(rc + 2), k + 2, x0, y0, a,
-                        tid, cp);
+                        tid, cp, c_pre);
+            c_pre = adj_coef_for(a, k + 3, tid);
         }
         const float4* L0 = slot(rc);
         const float4* Lp = slot(rc + 1);

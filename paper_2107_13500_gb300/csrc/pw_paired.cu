@@ -92,12 +92,21 @@ __device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
     return cp;
 }
 
+// Vertical coefficient tid (tzc1, tzc2, tzd1, tzd2) of level lev for threads
+// 0..3, 0 elsewhere.
+__device__ __forceinline__ double coef_for(const FwdArgs& a, int lev, int tid) {
+    if (tid >= 4) return 0.0;
+    const double* arr = tid == 0 ? a.tzc1 : tid == 1 ? a.tzc2 : tid == 2 ? a.tzd1 : a.tzd2;
+    return __ldg(arr + lev);
+}
+
 // Split load `seq` (level `lev`) into pair slot `slot`: item (row, x') of a
 // field takes the doubles of columns x0 + x' (lane A) and x0 + x' + kHalf
 // (lane B) of its box. Threads 0..3 also split the level's four vertical
-// coefficients into the same slot.
+// coefficients, given in `coef` (loaded one conversion earlier), into the
+// same slot.
 __device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, long long seq, int lev,
-                                              int slot, const FwdArgs& a, int tid, const ConvPlan& cp) {
+                                              int slot, const FwdArgs& a, int tid, const ConvPlan& cp, double coef) {
     float4* dst = ps.pairs + (slot % kPL) * 3 * kBoxItems;
     const double* base = ring.template box<double>(seq, 0) + a.xoff;
 #pragma unroll
@@ -110,8 +119,7 @@ __device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const Pai
         }
     }
     if (tid < 4) {
-        const double* arr = tid == 0 ? a.tzc1 : tid == 1 ? a.tzc2 : tid == 2 ? a.tzd1 : a.tzd2;
-        const pf p = split_double(__ldg(arr + lev));
+        const pf p = split_double(coef);
         ps.coef[(slot % kPL) * 4 + tid] = make_float4(p.h, p.h, p.l, p.l);
     }
 }
@@ -161,9 +169,11 @@ __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtenso
     // as its level is split; the step at relative level r splits r+2.
     const int pre = nl < kPL ? nl : kPL;
     bool bad = false, abort = false;
+    double c_pre = coef_for(a, lo, tid);  // next level's coefficient, one conversion ahead
     for (int r = 0; r < pre && !abort; ++r) {
         bad |= !ring.wait(s0 + r);
-        convert_level(ring, ps, s0 + r, lo + r, r, a, tid, cp);
+        convert_level(ring, ps, s0 + r, lo + r, r, a, tid, cp, c_pre);
+        c_pre = (lo + r + 1 <= hi) ? coef_for(a, lo + r + 1, tid) : 0.0;
         abort = __syncthreads_or(bad);  // load r's stage is free again
         if (!abort && tid == 0 && issued < nl) {
             fence_proxy_async_smem();
@@ -208,7 +218,8 @@ __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtenso
         if (r + 2 < nl) {
             // split relative level r+2 into the slot of r-1 (freed by the last barrier)
             bad |= !ring.wait(s0 + r + 2);
-            convert_level(ring, ps, s0 + r + 2, k + 2, r + 2, a, tid, cp);
+            convert_level(ring, ps, s0 + r + 2, k + 2, r + 2, a, tid, cp, c_pre);
+            c_pre = (k + 3 <= hi) ? coef_for(a, k + 3, tid) : 0.0;
         }
         const float4* U = ps.field(r, 0);
         const float4* V = ps.field(r, 1);

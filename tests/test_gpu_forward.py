@@ -80,6 +80,20 @@ def test_degenerate_shapes(gpu, oracle_lib, mode, shape):
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
+@pytest.mark.parametrize("shape", [(40, 8, 300), (17, 5, 129)])
+def test_tall_columns_many_level_chunks(gpu, oracle_lib, mode, shape):
+    """Few tiles and many levels: the launch cuts each column into many short
+    level chunks (up to 64), so most chunk boundaries, with their re-read
+    neighbour levels, fall inside the domain."""
+    nx, ny, nz = shape
+    dz = synth.dz_stretched(nz, 10.0, 1.01)
+    rho, rhon = synth.density_exponential(dz)
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=nz)
+    g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 50.0, 50.0, dz, rho, rhon, oracle_lib=oracle_lib)
+    compare_f64(g, o, a, nx, ny)
+
+
+@pytest.mark.parametrize("mode", F64_MODES)
 def test_integer_inputs_bit_exact(gpu, oracle_lib, mode):
     """Integer winds, dyadic coefficients: no operation of either side
     rounds, so the GPU must equal the oracle bit for bit."""

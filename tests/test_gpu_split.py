@@ -78,7 +78,7 @@ def test_split_small_iid(gpu, oracle_lib):
 
 @pytest.mark.parametrize("aligned", [True, False])
 @pytest.mark.parametrize("shape", [(37, 13, 5), (100, 17, 11), (31, 7, 3), (1, 1, 2), (5, 3, 1), (66, 9, 6),
-                                   (129, 5, 4)])
+                                   (129, 5, 4), (40, 8, 150)])
 def test_split_ragged_modes_density(gpu, oracle_lib, shape, aligned):
     """Smooth winds with a 5 m/s mean (where the split matters), stretched
     grid with density, partial tiles and strips, degenerate heights, both
