@@ -477,6 +477,17 @@ def extra_modes(torch, pw, oracle, args, sets16, c16, cfg16, ref16, ab16, peak):
                       "error_vs_oracle": error_stats(g, ref, ab, nx, ny)}
 
     if sets16[0][0][0].dtype == torch.float64:
+        # boundary helpers, timed apart from the headline: the periodic halo
+        # fill and the mean/perturbation split (12 B/pt: read 8, write 4)
+        t = fin16[0]
+        fp_buf = pw.empty_field(nx, ny, nz, torch.float32)
+        mean_buf = torch.empty(nz, dtype=torch.float64, device=t.device)
+        halo_ms = time_launches(torch, lambda _: pw.fill_periodic_halo(t, nx, ny), steps, 3, 1)
+        split_ms = time_launches(torch, lambda _: pw.split_field(t, nx, ny, out=fp_buf, mean=mean_buf), steps, 3, 1)
+        res["16m_helpers_per_field"] = {
+            "fill_periodic_halo_us": halo_ms * 1e3,
+            "split_field_us": split_ms * 1e3,
+            "split_field_GB_s": 12 * nx * ny * nz / (split_ms * 1e-3) / 1e9}
         for mode in ("f64", "paired", "split"):
             if mode == "split":
                 fp, means = zip(*(pw.split_field(t, nx, ny) for t in fin16))

@@ -8,6 +8,7 @@
 // Helpers: periodic halo fill and the per-level mean/perturbation split.
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cooperative_groups.h>
 #include <stdint.h>
 
 #include "pw_common.cuh"
@@ -15,6 +16,8 @@
 #include "pw_ring.cuh"
 
 namespace pw {
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // Native FP64 forward kernel.
@@ -210,44 +213,63 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 }
 
 // ---------------------------------------------------------------------------
-// Per-level mean and float perturbation. One CTA per level; each thread sums
-// a fixed strided subset of the interior in FP64, then a fixed-shape tree
-// adds the partial sums, so the result does not depend on scheduling.
+// Per-level mean and float perturbation. A cluster of kSplitCluster CTAs
+// takes one level: each CTA sums its share of the interior rows in FP64
+// (each thread a fixed strided subset, then a fixed-shape tree), the CTAs
+// add the cluster's partial sums in rank order through distributed shared
+// memory, and each then writes the perturbations of its share of the rows
+// (halo included). The result does not depend on scheduling.
 
-constexpr int kSplitThreads = 1024;
+constexpr int kSplitThreads = 512, kSplitCluster = 8;
 
-__global__ void __launch_bounds__(kSplitThreads) split_field_kernel(const double* __restrict__ f, long long fsy,
-                                                                    long long fsz, float* __restrict__ fp,
-                                                                    long long psy, long long psz, int nx, int ny,
-                                                                    double* __restrict__ mean) {
+__global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitThreads)
+    split_field_kernel(const double* __restrict__ f, long long fsy, long long fsz, float* __restrict__ fp,
+                       long long psy, long long psz, int nx, int ny, double* __restrict__ mean) {
     __shared__ double part[kSplitThreads];
-    const int k = blockIdx.x;
+    __shared__ double cta_sum;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int k = blockIdx.y;
     const double* lev = f + (size_t)k * (size_t)fsz;
-    const long long n = (long long)nx * ny;
+    // interior rows [r0, r1) of this CTA
+    const int r0 = 1 + (int)((long long)ny * rank / kSplitCluster);
+    const int r1 = 1 + (int)((long long)ny * (rank + 1) / kSplitCluster);
     double s = 0.0;
-    for (long long t = threadIdx.x; t < n; t += kSplitThreads) {
-        const int jj = 1 + (int)(t / nx), ii = 1 + (int)(t % nx);
-        s += lev[(size_t)jj * (size_t)fsy + ii];
+    for (int j = r0; j < r1; ++j) {
+        const double* row = lev + (size_t)j * (size_t)fsy;
+        for (int i = 1 + tid; i <= nx; i += kSplitThreads) s += row[i];
     }
-    part[threadIdx.x] = s;
+    part[tid] = s;
     __syncthreads();
     for (int h = kSplitThreads / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) part[threadIdx.x] += part[threadIdx.x + h];
+        if (tid < h) part[tid] += part[tid + h];
         __syncthreads();
     }
-    const double m = part[0] / (double)n;
-    if (threadIdx.x == 0) mean[k] = m;
+    if (tid == 0) cta_sum = part[0];
+    cluster.sync();  // every CTA's partial sum is in place
+    if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kSplitCluster; ++q) t += *cluster.map_shared_rank(&cta_sum, q);
+        part[0] = t / ((double)nx * (double)ny);
+    }
+    __syncthreads();
+    const double m = part[0];
+    cluster.sync();  // no CTA leaves while another still reads its partial sum
+    if (rank == 0 && tid == 0) mean[k] = m;
     float* out = fp + (size_t)k * (size_t)psz;
-    const long long nh = (long long)(nx + 2) * (ny + 2);
-    for (long long t = threadIdx.x; t < nh; t += kSplitThreads) {
-        const int jj = (int)(t / (nx + 2)), ii = (int)(t % (nx + 2));
-        out[(size_t)jj * (size_t)psy + ii] = (float)(lev[(size_t)jj * (size_t)fsy + ii] - m);
+    const int h0 = (int)((long long)(ny + 2) * rank / kSplitCluster);
+    const int h1 = (int)((long long)(ny + 2) * (rank + 1) / kSplitCluster);
+    for (int j = h0; j < h1; ++j) {
+        const double* row = lev + (size_t)j * (size_t)fsy;
+        float* orow = out + (size_t)j * (size_t)psy;
+        for (int i = tid; i < nx + 2; i += kSplitThreads) orow[i] = (float)(row[i] - m);
     }
 }
 
 cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, float* fp, long long psy,
                                long long psz, int nx, int ny, int nz, double* mean, cudaStream_t st) {
-    split_field_kernel<<<nz, kSplitThreads, 0, st>>>(f, fsy, fsz, fp, psy, psz, nx, ny, mean);
+    split_field_kernel<<<dim3(kSplitCluster, nz), kSplitThreads, 0, st>>>(f, fsy, fsz, fp, psy, psz, nx, ny, mean);
     return cudaGetLastError();
 }
 
