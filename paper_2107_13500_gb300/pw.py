@@ -301,13 +301,18 @@ def advect(u, v, w, coeffs: Coefficients, nx, ny, mode="paired", split_table=Non
 
 class HostPipeline:
     """Device staging buffers and three streams for advect_host: reuse one
-    across calls on same-shaped fields."""
+    across calls on same-shaped fields. It remembers when the previous call's
+    kernels finished (its device inputs are free) and when its outputs left
+    the device (its device outputs are free), so that the next call's input
+    copies overlap the previous call's output copies."""
 
     def __init__(self, nx, ny, nz, dtype=None, device="cuda"):
         import torch
         dtype = dtype or torch.float64
         self.dev = [empty_field(nx, ny, nz, dtype, device) for _ in range(6)]
         self.streams = [torch.cuda.Stream(device=device) for _ in range(3)]
+        self.compute_done = None
+        self.d2h_done = None
 
 
 def pinned_field(nx, ny, nz, dtype=None):
@@ -322,7 +327,10 @@ def advect_host(u_h, v_h, w_h, coeffs: Coefficients, nx, ny, mode="paired", out_
                 nchunks=8, split_table=None, wait=True):
     """pw_advect on pinned host fields with chunked, overlapped transfers
     (pw_advect_host_chunked). Returns the host outputs; with wait=True the
-    call returns after they have arrived."""
+    call returns after they have arrived, otherwise the caller's current
+    stream is ordered after their arrival. The host inputs are read when the
+    input copies run, which may be before earlier work on the caller's
+    stream: they must be complete in host memory when the call is made."""
     import torch
     lib = load_library()
     dt = MODES[mode]
@@ -341,14 +349,25 @@ def advect_host(u_h, v_h, w_h, coeffs: Coefficients, nx, ny, mode="paired", out_
     vp = ctypes.c_void_p
     sh, sc, sd = pipeline.streams
     cur = torch.cuda.current_stream()
-    for s in pipeline.streams:
-        s.wait_stream(cur)
+    # input copies: only the staging inputs must be free (previous kernels done)
+    if pipeline.compute_done is not None:
+        sh.wait_event(pipeline.compute_done)
+    # kernels: the caller's device work (coefficients, tables) and the
+    # previous call's outputs drained from the staging outputs
+    sc.wait_stream(cur)
+    if pipeline.d2h_done is not None:
+        sc.wait_event(pipeline.d2h_done)
+    sd.wait_stream(cur)
     _check(lib.pw_advect_host_chunked(dt, *(vp(t.data_ptr()) for t in (u_h, v_h, w_h) + tuple(out_host)),
                                       *(vp(t.data_ptr()) for t in pipeline.dev), ctypes.byref(c), ctypes.byref(d),
                                       None if split_table is None else vp(split_table.data_ptr()), int(nchunks),
                                       vp(sh.cuda_stream), vp(sc.cuda_stream), vp(sd.cuda_stream)))
-    for s in pipeline.streams:
-        cur.wait_stream(s)
+    pipeline.compute_done = torch.cuda.Event()
+    pipeline.compute_done.record(sc)
+    pipeline.d2h_done = torch.cuda.Event()
+    pipeline.d2h_done.record(sd)
+    # the output copies follow every kernel and input copy of the call
+    cur.wait_event(pipeline.d2h_done)
     if wait:
         sd.synchronize()
     return out_host

@@ -160,6 +160,34 @@ def test_guard_bands_and_halo_untouched(gpu, oracle_lib, mode, aligned):
         assert np.all(bits[mask] == int(canary.view(torch.int64))), "a cell outside the interior was written"
 
 
+def test_host_chunked_back_to_back_calls(gpu):
+    """Consecutive asynchronous advect_host calls on one pipeline overlap
+    (the next call's input copies run while the previous call's outputs
+    drain); each call's outputs must still equal a device call on its own
+    inputs."""
+    import torch
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 96, 40, 24
+    dz = synth.dz_stretched(nz)
+    c = pw.make_coeffs(nz, 50.0, 50.0, dz).to_device()
+    pipe = pw.HostPipeline(nx, ny, nz)
+    calls = []
+    for seed in (31, 32, 33):
+        fields = synth.fields_modes(nx, ny, nz, 50.0, 50.0, dz, seed=seed)
+        host = [pw.pinned_field(nx, ny, nz) for _ in range(3)]
+        for h, a in zip(host, fields):
+            h[:, :, : nx + 2] = torch.from_numpy(a[:, :, : nx + 2])
+        out = tuple(pw.pinned_field(nx, ny, nz) for _ in range(3))
+        pw.advect_host(*host, c, nx, ny, mode="paired", out_host=out, pipeline=pipe, nchunks=6, wait=False)
+        calls.append((fields, out))
+    torch.cuda.synchronize()
+    for fields, out in calls:
+        want = pw.advect(*[pw.field_from_numpy(a, nx) for a in fields], c, nx, ny, mode="paired")
+        torch.cuda.synchronize()
+        for g, w_ in zip(out, want):
+            assert torch.equal(g[:, 1:ny + 1, 1:nx + 1], w_.cpu()[:, 1:ny + 1, 1:nx + 1])
+
+
 def test_periodic_halo_fill_matches_numpy(gpu):
     """pw_fill_periodic_halo against numpy's wrap padding of the interior."""
     import torch
