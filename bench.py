@@ -354,6 +354,18 @@ def main():
     if status != 0:
         raise SystemExit(f"kernel reported device status {status}")
     ms, value = replica_throughput(ms, pts, dist, device="cuda")
+    # per-launch distribution (a separate loop, one event pair per launch;
+    # the headline above is the K-step mean the contract asks for)
+    nlaunch = 50
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nlaunch)]
+    for n, (a0, a1) in enumerate(evs):
+        a0.record(stream)
+        step(n % nsets)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    per_launch = sorted(a0.elapsed_time(a1) for a0, a1 in evs)
+    launch_stats = {"launches": nlaunch, "median_ms": statistics.median(per_launch),
+                    "p10_ms": per_launch[nlaunch // 10], "p90_ms": per_launch[(9 * nlaunch) // 10]}
 
     # end to end through the public API: pinned host inputs -> device ->
     # pw_advect -> host outputs, inside the timed region. Overlapped form:
@@ -431,6 +443,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": roofline,
         "hbm_roofline_frac": achieved / peak,
+        "launch_ms": launch_stats,
         "e2e": e2e,
         "gpu_launches": args.steps,
         "clocks": clocks,
