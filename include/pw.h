@@ -236,7 +236,8 @@ size_t pw_batch_plan_bytes(int n);
  * PW_F32 / PW_F32_SPLIT (points per CTA, TMA ring depth): 0 = 128x4, 4 levels;
  * 1 = 64x4; 2 = 32x8; 3 = 64x8; 4 = 32x16; 5 = 128x2 (all 4 levels);
  * 6 = 64x4, 3 levels; 7 = 64x4, 6 levels.
- * PW_F64_PAIRED: 1 variant. PW_F64: 0 (not batched). */
+ * PW_F64_PAIRED: 0 = 32x8, 2 levels; 1 = 32x4; 2 = 32x16 (2 levels);
+ * 3 = 32x8, 3 levels. PW_F64: 0 (not batched). */
 int pw_variant_count(pw_dtype dtype);
 
 /*

@@ -443,7 +443,7 @@ extern "C" int pw_variant_count(pw_dtype dtype) {
     switch (dtype) {
         case PW_F32:
         case PW_F32_SPLIT: return pw::split_variant_count();
-        case PW_F64_PAIRED: return 1;
+        case PW_F64_PAIRED: return pw::paired_variant_count();
         default: return 0;
     }
 }
@@ -461,7 +461,7 @@ extern "C" int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain* doms, 
         return fail(PW_EINVAL, "%s: plan_bytes %zu < %zu", who, plan_bytes, pw::batch_plan_bytes(n));
     if (((uintptr_t)plan_host) % 64 != 0) return fail(PW_EINVAL, "%s: plan_host must be 64-byte aligned", who);
     const int es = elem_size(dtype);
-    const pw::TileShape shp = dtype == PW_F64_PAIRED ? pw::fwd_paired_shape() : pw::fwd_split_shape_variant(variant);
+    const pw::TileShape shp = dtype == PW_F64_PAIRED ? pw::fwd_paired_shape_variant(variant) : pw::fwd_split_shape_variant(variant);
     // tallest domains first: their tiles take longest, so they start first
     std::vector<int> order(n);
     for (int d = 0; d < n; ++d) order[d] = d;
@@ -549,7 +549,7 @@ extern "C" int pw_advect_batched(pw_dtype dtype, int variant, void* plan_dev, lo
     pw::BatchPlan* plan = static_cast<pw::BatchPlan*>(plan_dev);
     cudaError_t e = cudaMemsetAsync(&plan->counter, 0, sizeof(plan->counter), st);
     if (e != cudaSuccess) return cuda_fail(e, who);
-    e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(plan, n_items, st)
+    e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(variant, plan, n_items, st)
                                : pw::launch_split_batched(variant, plan, n_items, st);
     if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;

@@ -129,7 +129,9 @@ TileShape fwd_split_shape_variant(int v);
 cudaError_t launch_fwd_split_variant(int v, const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                                      const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_split_batched(int v, BatchPlan* plan, long long n_items, cudaStream_t st);
-cudaError_t launch_paired_batched(BatchPlan* plan, long long n_items, cudaStream_t st);
+int paired_variant_count();
+TileShape fwd_paired_shape_variant(int v);
+cudaError_t launch_paired_batched(int v, BatchPlan* plan, long long n_items, cudaStream_t st);
 
 cudaError_t launch_fwd_f64(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                            const FwdArgs& a, cudaStream_t st);

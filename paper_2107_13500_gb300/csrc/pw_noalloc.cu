@@ -93,7 +93,7 @@ extern "C" int pw_advect_batched_noalloc(pw_dtype dtype, int variant, const void
     e = cudaMemcpyAsync(scratch, plan_host, need, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(&plan->counter, 0, sizeof(plan->counter), st);
     if (e != cudaSuccess) return fail(PW_ECUDA, "pw_advect_batched_noalloc: copying the plan failed");
-    e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(plan, n_items, st)
+    e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(variant, plan, n_items, st)
                                : pw::launch_split_batched(variant, plan, n_items, st);
     if (e != cudaSuccess) return fail(PW_ECUDA, "pw_advect_batched_noalloc: launch failed");
     return PW_OK;

@@ -33,29 +33,60 @@ namespace pw {
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kS = 2, kPL = 3;  // TMA stages, pair-ring levels
-using Shape = RingShape<double, kTX, kTY, kS>;
-constexpr int kHalf = kTX / 2;          // x distance from A to B; threads per tile row
-constexpr int kNT = kHalf * kTY;
-constexpr int kHX = kHalf + 2;          // pair-box row: columns x' = 0..kHalf+1 of both halves
-constexpr int kBoxItems = Shape::BY * kHX;  // float4 {hA, hB, lA, lB} per field and level
-static_assert((kHX - 1) + kHalf + Shape::XOFF_MAX < Shape::BX, "both halves' columns must lie inside the TMA box row");
-// pair ring: [kPL levels][3 fields][kBoxItems] float4, then [kPL levels][4]
-// coefficients as float4 {h, h, l, l}
-constexpr int kPairBytes = kPL * 3 * kBoxItems * 16;
-constexpr int kCoefBytes = kPL * 4 * 16;
-// ring stages | ring barriers (S x 8 B, padded to 64 B) | pairs | coefficient
-// pairs | work-item slot, plus 128 B of slack for aligning the ring base
-constexpr int kPairOffset = Shape::S * Shape::STAGE_BYTES + 64;
-constexpr int kItemOffset = kPairOffset + kPairBytes + kCoefBytes;
-constexpr int kSmemBytes = kItemOffset + 16 + 128;
-static_assert(Shape::S * 8 <= 64, "ring barriers must fit before the pair buffers");
-// A stage is reissued once its level is split, so two stages keep one load
-// in flight while the other level is split.
-static_assert(kS >= 2, "the TMA ring needs a load in flight behind the one being split");
-// CTAs per SM the shared memory allows (1 KB per CTA is reserved by the
-// hardware); the register budget follows from it.
-constexpr int kMinBlocks = (227 * 1024) / (kSmemBytes + 1024);
+// Tile height and TMA stages of a variant (the tile is 32 points wide: the
+// two lanes of a thread are 16 apart).
+template <int TY_, int S_>
+struct PairedCfg {
+    static constexpr int kTX = 32, kTY = TY_, kS = S_, kPL = 3;  // TMA stages, pair-ring levels
+    using Shape = RingShape<double, kTX, kTY, kS>;
+    static constexpr int kHalf = kTX / 2;          // x distance from A to B; threads per tile row
+    static constexpr int kNT = kHalf * kTY;
+    static constexpr int kHX = kHalf + 2;          // pair-box row: columns x' = 0..kHalf+1 of both halves
+    static constexpr int kBoxItems = Shape::BY * kHX;  // float4 {hA, hB, lA, lB} per field and level
+    // pair ring: [kPL levels][3 fields][kBoxItems] float4, then [kPL levels][4]
+    // coefficients as float4 {h, h, l, l}
+    static constexpr int kPairBytes = kPL * 3 * kBoxItems * 16;
+    static constexpr int kCoefBytes = kPL * 4 * 16;
+    // ring stages | ring barriers (S x 8 B, padded to 64 B) | pairs | coefficient
+    // pairs | work-item slot, plus 128 B of slack for aligning the ring base
+    static constexpr int kPairOffset = Shape::S * Shape::STAGE_BYTES + 64;
+    static constexpr int kItemOffset = kPairOffset + kPairBytes + kCoefBytes;
+    static constexpr int kSmemBytes = kItemOffset + 16 + 128;
+    // CTAs per SM the shared memory allows (1 KB per CTA is reserved by the
+    // hardware); the register budget follows from it.
+    static constexpr int kMinBlocks = (227 * 1024) / (kSmemBytes + 1024);
+    // split work per thread and level (see ConvPlan)
+    static constexpr int kConvIters = (3 * kBoxItems + kNT - 1) / kNT;
+    static_assert((kHX - 1) + kHalf + Shape::XOFF_MAX < Shape::BX,
+                  "both halves' columns must lie inside the TMA box row");
+    static_assert(Shape::S * 8 <= 64, "ring barriers must fit before the pair buffers");
+    // A stage is reissued once its level is split, so two stages keep one load
+    // in flight while the other level is split.
+    static_assert(kS >= 2, "the TMA ring needs a load in flight behind the one being split");
+    static_assert(Shape::BOX_STRIDE % 8 == 0, "box stride in doubles");
+};
+
+// The batched variants (the autotuner's search space); variant 0 also serves
+// pw_advect.
+using PV0 = PairedCfg<8, 2>;
+using PV1 = PairedCfg<4, 2>;
+using PV2 = PairedCfg<16, 2>;
+using PV3 = PairedCfg<8, 3>;
+
+// The device code of one variant: constants of C in scope.
+template <class C>
+struct PairedK : C {
+    using typename C::Shape;
+    using C::kTX;
+    using C::kTY;
+    using C::kPL;
+    using C::kHalf;
+    using C::kNT;
+    using C::kHX;
+    using C::kBoxItems;
+    using C::kPairOffset;
+    using C::kItemOffset;
+    using C::kConvIters;
 
 struct PairSmem {
     float4* pairs;    // [kPL][3][kBoxItems]
@@ -74,13 +105,11 @@ struct PairSmem {
 // n = (field, row, x') of the pair slot). Which doubles of a stage those are
 // does not depend on the level or the tile, so each thread works out their
 // offsets once.
-constexpr int kConvIters = (3 * kBoxItems + kNT - 1) / kNT;
-static_assert(Shape::BOX_STRIDE % 8 == 0, "box stride in doubles");
 struct ConvPlan {
     int off[kConvIters];  // offset (doubles) in a stage of lane A's value of item tid + q*kNT, xoff = 0
 };
 
-__device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
+static __device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
     ConvPlan cp;
 #pragma unroll
     for (int q = 0; q < kConvIters; ++q) {
@@ -94,7 +123,7 @@ __device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
 
 // Vertical coefficient tid (tzc1, tzc2, tzd1, tzd2) of level lev for threads
 // 0..3, 0 elsewhere.
-__device__ __forceinline__ double coef_for(const FwdArgs& a, int lev, int tid) {
+static __device__ __forceinline__ double coef_for(const FwdArgs& a, int lev, int tid) {
     if (tid >= 4) return 0.0;
     const double* arr = tid == 0 ? a.tzc1 : tid == 1 ? a.tzc2 : tid == 2 ? a.tzd1 : a.tzd2;
     return __ldg(arr + lev);
@@ -105,7 +134,7 @@ __device__ __forceinline__ double coef_for(const FwdArgs& a, int lev, int tid) {
 // (lane B) of its box. Threads 0..3 also split the level's four vertical
 // coefficients, given in `coef` (loaded one conversion earlier), into the
 // same slot.
-__device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, long long seq, int lev,
+static __device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, long long seq, int lev,
                                               int slot, const FwdArgs& a, int tid, const ConvPlan& cp, double coef) {
     float4* dst = ps.pairs + (slot % kPL) * 3 * kBoxItems;
     const double* base = ring.template box<double>(seq, 0) + a.xoff;
@@ -124,20 +153,20 @@ __device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const Pai
     }
 }
 
-__device__ __forceinline__ pf2 ld(const float4* b, int idx) {
+static __device__ __forceinline__ pf2 ld(const float4* b, int idx) {
     const float4 v = b[idx];
     return {make_float2(v.x, v.y), make_float2(v.z, v.w)};
 }
 
-__device__ __forceinline__ double join_a(const pf2& p) { return pair_to_double(pf{p.h.x, p.l.x}); }
-__device__ __forceinline__ double join_b(const pf2& p) { return pair_to_double(pf{p.h.y, p.l.y}); }
+static __device__ __forceinline__ double join_a(const pf2& p) { return pair_to_double(pf{p.h.x, p.l.x}); }
+static __device__ __forceinline__ double join_b(const pf2& p) { return pair_to_double(pf{p.h.y, p.l.y}); }
 
 // One tile (bx, by) of domain `a`, output levels kb..ke-1 (a k-chunk; the
 // chunk reads one level below and one above). `seq` is the CTA's running
 // load count. Loads, pair slots and coefficient slots are numbered relative
 // to the lowest level read, lo. Returns false if a bounded wait expired
 // (status set, copies drained).
-__device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtensorMap* mu, const CUtensorMap* mv,
+static __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtensorMap* mu, const CUtensorMap* mv,
                             const CUtensorMap* mw, const FwdArgs& a, int bx, int by, int kb, int ke,
                             long long& seq, int tid, const ConvPlan& cp) {
     constexpr int S = Shape::S;
@@ -294,21 +323,24 @@ __device__ bool paired_tile(Ring<Shape>& ring, const PairSmem& ps, const CUtenso
     return true;
 }
 
-__device__ __forceinline__ void setup_smem(unsigned char* raw, Ring<Shape>& ring, PairSmem& ps) {
+static __device__ __forceinline__ void setup_smem(unsigned char* raw, Ring<Shape>& ring, PairSmem& ps) {
     ring.setup(raw);
     ps.pairs = reinterpret_cast<float4*>(ring.base + kPairOffset);
     ps.coef = ps.pairs + kPL * 3 * kBoxItems;
     ps.item = reinterpret_cast<long long*>(ring.base + kItemOffset);
 }
+};
 
-__global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
-                                                               const __grid_constant__ CUtensorMap mv,
-                                                               const __grid_constant__ CUtensorMap mw,
-                                                               const FwdArgs a) {
+template <class C>
+__global__ void __launch_bounds__(C::kNT, C::kMinBlocks) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
+                                                                           const __grid_constant__ CUtensorMap mv,
+                                                                           const __grid_constant__ CUtensorMap mw,
+                                                                           const FwdArgs a) {
+    using K = PairedK<C>;
     extern __shared__ unsigned char smem_raw[];
-    Ring<Shape> ring;
-    PairSmem ps;
-    setup_smem(smem_raw, ring, ps);
+    Ring<typename C::Shape> ring;
+    typename K::PairSmem ps;
+    K::setup_smem(smem_raw, ring, ps);
     const int tid = threadIdx.x;
     if (tid == 0) {
         prefetch_tensormap(&mu);
@@ -320,26 +352,28 @@ __global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_kernel(const __gri
     long long seq = 0;
     const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
     const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
-    const ConvPlan cp = make_conv_plan(tid);
-    (void)paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid, cp);
+    const typename K::ConvPlan cp = K::make_conv_plan(tid);
+    (void)K::paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid, cp);
 }
 
 // Persistent form over a batch plan: work items (one tile of one domain)
 // come from the plan's counter, at most n_items iterations.
-__global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_batched(BatchPlan* plan) {
+template <class C>
+__global__ void __launch_bounds__(C::kNT, C::kMinBlocks) fwd_paired_batched(BatchPlan* plan, int variant) {
+    using K = PairedK<C>;
     extern __shared__ unsigned char smem_raw[];
-    Ring<Shape> ring;
-    PairSmem ps;
-    setup_smem(smem_raw, ring, ps);
+    Ring<typename C::Shape> ring;
+    typename K::PairSmem ps;
+    K::setup_smem(smem_raw, ring, ps);
     const int tid = threadIdx.x;
-    if (plan->variant != 0 || plan->dtype != PW_F64_PAIRED) {
+    if (plan->variant != variant || plan->dtype != PW_F64_PAIRED) {
         if (tid == 0) atomicOr(&tu_status, kStatusBadPlan);
         return;
     }
     if (tid == 0) ring.init_barriers();
     __syncthreads();
     const long long n_items = plan->n_items;
-    const ConvPlan cp = make_conv_plan(tid);
+    const typename K::ConvPlan cp = K::make_conv_plan(tid);
     long long seq = 0;
     for (long long it = 0; it < n_items; ++it) {
         if (tid == 0) *ps.item = (long long)atomicAdd(&plan->counter, 1ull);
@@ -356,8 +390,40 @@ __global__ void __launch_bounds__(kNT, kMinBlocks) fwd_paired_batched(BatchPlan*
         const int ch = (int)(t / tiles), tt = (int)(t % tiles);
         const int kb = (int)((long long)args.nz * ch / kchunks);
         const int ke = (int)((long long)args.nz * (ch + 1) / kchunks);
-        if (!paired_tile(ring, ps, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid, cp)) break;
+        if (!K::paired_tile(ring, ps, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid, cp))
+            break;
     }
+}
+
+template <class C>
+TileShape paired_shape_of() {
+    return TileShape{C::kTX, C::kTY, C::Shape::BX, C::Shape::BY, C::kSmemBytes, C::kNT};
+}
+
+template <class C>
+cudaError_t launch_one(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw, const FwdArgs& a,
+                       cudaStream_t st) {
+    auto kern = fwd_paired_kernel<C>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)((a.nx + C::kTX - 1) / C::kTX) * ((a.ny + C::kTY - 1) / C::kTY);
+    int chunks = 1;
+    if ((e = choose_kchunks(kern, C::kNT, C::kSmemBytes, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess) return e;
+    dim3 grid((a.nx + C::kTX - 1) / C::kTX, (a.ny + C::kTY - 1) / C::kTY, chunks);
+    kern<<<grid, C::kNT, C::kSmemBytes, st>>>(mu, mv, mw, a);
+    return cudaGetLastError();
+}
+
+template <class C>
+cudaError_t launch_batched_cfg(int v, BatchPlan* plan, long long n_items, cudaStream_t st) {
+    auto kern = fwd_paired_batched<C>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    long long grid = 0;
+    if ((e = persistent_grid(kern, C::kNT, C::kSmemBytes, n_items, &grid)) != cudaSuccess) return e;
+    if (grid < 1) return cudaSuccess;
+    kern<<<(unsigned)grid, C::kNT, C::kSmemBytes, st>>>(plan, v);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -366,29 +432,31 @@ cudaError_t read_and_clear_status_paired(unsigned int* status, cudaStream_t st) 
     return read_and_clear_tu_status(status, st);
 }
 
-TileShape fwd_paired_shape() { return TileShape{kTX, kTY, Shape::BX, Shape::BY, kSmemBytes, kNT}; }
+int paired_variant_count() { return 4; }
+
+TileShape fwd_paired_shape_variant(int v) {
+    switch (v) {
+        case 1: return paired_shape_of<PV1>();
+        case 2: return paired_shape_of<PV2>();
+        case 3: return paired_shape_of<PV3>();
+        default: return paired_shape_of<PV0>();
+    }
+}
+
+TileShape fwd_paired_shape() { return fwd_paired_shape_variant(0); }
 
 cudaError_t launch_fwd_paired(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
                               const FwdArgs& a, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(fwd_paired_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    const long long tiles = (long long)((a.nx + kTX - 1) / kTX) * ((a.ny + kTY - 1) / kTY);
-    int chunks = 1;
-    if ((e = choose_kchunks(fwd_paired_kernel, kNT, kSmemBytes, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess) return e;
-    dim3 grid((a.nx + kTX - 1) / kTX, (a.ny + kTY - 1) / kTY, chunks);
-    fwd_paired_kernel<<<grid, kNT, kSmemBytes, st>>>(mu, mv, mw, a);
-    return cudaGetLastError();
+    return launch_one<PV0>(mu, mv, mw, a, st);
 }
 
-cudaError_t launch_paired_batched(BatchPlan* plan, long long n_items, cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(fwd_paired_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    long long grid = 0;
-    if ((e = persistent_grid(fwd_paired_batched, kNT, kSmemBytes, n_items, &grid)) != cudaSuccess) return e;
-    if (grid < 1) return cudaSuccess;
-    fwd_paired_batched<<<(unsigned)grid, kNT, kSmemBytes, st>>>(plan);
-    return cudaGetLastError();
+cudaError_t launch_paired_batched(int v, BatchPlan* plan, long long n_items, cudaStream_t st) {
+    switch (v) {
+        case 1: return launch_batched_cfg<PV1>(1, plan, n_items, st);
+        case 2: return launch_batched_cfg<PV2>(2, plan, n_items, st);
+        case 3: return launch_batched_cfg<PV3>(3, plan, n_items, st);
+        default: return launch_batched_cfg<PV0>(0, plan, n_items, st);
+    }
 }
 
 }  // namespace pw

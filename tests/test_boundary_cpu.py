@@ -184,7 +184,7 @@ def test_batch_plan_validation_without_device(lib):
     import ctypes
     from paper_2107_13500_gb300 import pw
     assert lib.pw_batch_plan_bytes(96) > lib.pw_batch_plan_bytes(1) > 0
-    assert lib.pw_variant_count(pw.PW_F32) == 8 and lib.pw_variant_count(pw.PW_F64_PAIRED) == 1
+    assert lib.pw_variant_count(pw.PW_F32) == 8 and lib.pw_variant_count(pw.PW_F64_PAIRED) == 4
     assert lib.pw_variant_count(pw.PW_F64) == 0
     nbytes = lib.pw_batch_plan_bytes(2)
     raw = np.zeros(nbytes + 128, dtype=np.uint8)
