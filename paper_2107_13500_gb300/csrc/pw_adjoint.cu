@@ -322,8 +322,15 @@ static_assert(PSh::BOX_STRIDE % 8 == 0, "box stride in doubles");
 // unit left of the tile), lane B kPHalf further
 static_assert((kPHX - 1) + 1 + PSh::XOFF_MAX + kPHalf < PSh::BX, "both halves must lie inside the box row");
 
-// Per-thread split work: item tid + q*kPNT of a level is (field, row, x');
-// offsets and positions depend on neither the level nor the tile.
+// Per-thread split work: item t' + q*kPNT of a level is (field, row, x'),
+// with t' = (tid + 64) mod kPNT, so the partial last round of items falls on
+// warps 2 and 3 while thread 0 issues the TMA loads and warp 1 splits the
+// level coefficients. Offsets and positions depend on neither the level nor
+// the tile.
+__device__ __forceinline__ int adj_conv_item(int tid, int q) { return (tid + 64) % kPNT + q * kPNT; }
+constexpr int kPCoefWarp = 1;
+static_assert(kPNT >= 128, "the split work is spread over four warps");
+
 struct AdjConvPlan {
     int off[kPConvIters];   // lane A's double offset in a stage (xoff = 0)
     int info[kPConvIters];  // field | row << 8 | x' << 16
@@ -333,7 +340,7 @@ __device__ __forceinline__ AdjConvPlan make_adj_conv_plan(int tid) {
     AdjConvPlan cp;
 #pragma unroll
     for (int q = 0; q < kPConvIters; ++q) {
-        const int n = tid + q * kPNT;
+        const int n = adj_conv_item(tid, q);
         const int f = n / kPItems, e = n - f * kPItems;
         const int row = e / kPHX, xp = e - row * kPHX;
         cp.off[q] = f * (PSh::BOX_STRIDE / 8) + row * PSh::BX + xp + 1;
@@ -342,15 +349,16 @@ __device__ __forceinline__ AdjConvPlan make_adj_conv_plan(int tid) {
     return cp;
 }
 
-// Coefficient n = tid of level lev for threads 0..6 (0 elsewhere and for
-// levels outside the domain).
+// Coefficient n of level lev for lane n = 0..6 of warp kPCoefWarp (0
+// elsewhere and for levels outside the domain).
 __device__ __forceinline__ double adj_coef_for(const AdjArgs& a, int lev, int tid) {
-    return (tid < 7 && lev >= 0 && lev < a.nz) ? level_coef(a, lev, tid) : 0.0;
+    const int n = tid - 32 * kPCoefWarp;
+    return ((unsigned)n < 7u && lev >= 0 && lev < a.nz) ? level_coef(a, lev, n) : 0.0;
 }
 
 // Split the level `lev` held in `stage` into pair slot `dst`; cotangent cells
-// outside the computed output points become (0, 0). Threads 0..6 also store
-// the level's seven coefficients (as for the FP64 kernel), given in `coef`
+// outside the computed output points become (0, 0). Lanes 0..6 of warp
+// kPCoefWarp also store the level's seven coefficients (as for the FP64 kernel), given in `coef`
 // (loaded one conversion earlier), as pairs {h, h, l, l}.
 __device__ __forceinline__ void adj_convert(const unsigned char* stage, float4* dst, float4* cdst, int lev,
                                             int x0, int y0, const AdjArgs& a, int tid, const AdjConvPlan& cp,
@@ -360,7 +368,7 @@ __device__ __forceinline__ void adj_convert(const unsigned char* stage, float4* 
     const bool w_ok = lev >= 1 && lev <= a.nz - 2; // sw: levels 1..nz-2
 #pragma unroll
     for (int q = 0; q < kPConvIters; ++q) {
-        const int n = tid + q * kPNT;
+        const int n = adj_conv_item(tid, q);
         if ((q + 1) * kPNT <= kFields * kPItems || n < kFields * kPItems) {
             const double* src = base + cp.off[q];
             double da = src[0], db = src[kPHalf];
@@ -377,9 +385,10 @@ __device__ __forceinline__ void adj_convert(const unsigned char* stage, float4* 
             dst[n] = make_float4(p0.h, p1.h, p0.l, p1.l);
         }
     }
-    if (tid < 7 && lev >= 0 && lev < a.nz) {
+    const int cn = tid - 32 * kPCoefWarp;
+    if ((unsigned)cn < 7u && lev >= 0 && lev < a.nz) {
         const pf p = split_double(coef);
-        cdst[tid] = make_float4(p.h, p.h, p.l, p.l);
+        cdst[cn] = make_float4(p.h, p.h, p.l, p.l);
     }
 }
 

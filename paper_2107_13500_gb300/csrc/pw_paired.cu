@@ -57,6 +57,11 @@ struct PairedCfg {
     static constexpr int kMinBlocks = (227 * 1024) / (kSmemBytes + 1024);
     // split work per thread and level (see ConvPlan)
     static constexpr int kConvIters = (3 * kBoxItems + kNT - 1) / kNT;
+    // Per-level extra work is spread over warps: thread 0 issues the TMA
+    // loads, warp kCoefWarp splits the four vertical coefficients, and the
+    // split items are rotated by one warp so the partial last round of items
+    // falls on the last warp.
+    static constexpr int kCoefWarp = kNT >= 96 ? 2 : 0;
     static_assert((kHX - 1) + kHalf + Shape::XOFF_MAX < Shape::BX,
                   "both halves' columns must lie inside the TMA box row");
     static_assert(Shape::S * 8 <= 64, "ring barriers must fit before the pair buffers");
@@ -87,6 +92,7 @@ struct PairedK : C {
     using C::kPairOffset;
     using C::kItemOffset;
     using C::kConvIters;
+    using C::kCoefWarp;
 
 struct PairSmem {
     float4* pairs;    // [kPL][3][kBoxItems]
@@ -101,19 +107,21 @@ struct PairSmem {
     }
 };
 
-// The split pass gives thread t the items t, t + kNT, ... of a level (item
-// n = (field, row, x') of the pair slot). Which doubles of a stage those are
-// does not depend on the level or the tile, so each thread works out their
-// offsets once.
+// The split pass gives thread t the items t', t' + kNT, ... of a level, with
+// t' = (t + 32) mod kNT (item n = (field, row, x') of the pair slot). Which
+// doubles of a stage those are does not depend on the level or the tile, so
+// each thread works out their offsets once.
 struct ConvPlan {
     int off[kConvIters];  // offset (doubles) in a stage of lane A's value of item tid + q*kNT, xoff = 0
 };
+
+static __device__ __forceinline__ int conv_item(int tid, int q) { return (tid + 32) % kNT + q * kNT; }
 
 static __device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
     ConvPlan cp;
 #pragma unroll
     for (int q = 0; q < kConvIters; ++q) {
-        const int n = tid + q * kNT;
+        const int n = conv_item(tid, q);
         const int f = n / kBoxItems, e = n - f * kBoxItems;
         const int row = e / kHX, xp = e - row * kHX;
         cp.off[q] = f * (Shape::BOX_STRIDE / 8) + row * Shape::BX + xp;
@@ -121,35 +129,37 @@ static __device__ __forceinline__ ConvPlan make_conv_plan(int tid) {
     return cp;
 }
 
-// Vertical coefficient tid (tzc1, tzc2, tzd1, tzd2) of level lev for threads
-// 0..3, 0 elsewhere.
+// Vertical coefficient n (tzc1, tzc2, tzd1, tzd2) of level lev for lane n =
+// 0..3 of warp kCoefWarp, 0 elsewhere.
 static __device__ __forceinline__ double coef_for(const FwdArgs& a, int lev, int tid) {
-    if (tid >= 4) return 0.0;
-    const double* arr = tid == 0 ? a.tzc1 : tid == 1 ? a.tzc2 : tid == 2 ? a.tzd1 : a.tzd2;
+    const int n = tid - 32 * kCoefWarp;
+    if ((unsigned)n >= 4u) return 0.0;
+    const double* arr = n == 0 ? a.tzc1 : n == 1 ? a.tzc2 : n == 2 ? a.tzd1 : a.tzd2;
     return __ldg(arr + lev);
 }
 
 // Split load `seq` (level `lev`) into pair slot `slot`: item (row, x') of a
 // field takes the doubles of columns x0 + x' (lane A) and x0 + x' + kHalf
-// (lane B) of its box. Threads 0..3 also split the level's four vertical
-// coefficients, given in `coef` (loaded one conversion earlier), into the
-// same slot.
+// (lane B) of its box. Lanes 0..3 of warp kCoefWarp also split the level's
+// four vertical coefficients, given in `coef` (loaded one conversion
+// earlier), into the same slot.
 static __device__ __forceinline__ void convert_level(const Ring<Shape>& ring, const PairSmem& ps, long long seq, int lev,
                                               int slot, const FwdArgs& a, int tid, const ConvPlan& cp, double coef) {
     float4* dst = ps.pairs + (slot % kPL) * 3 * kBoxItems;
     const double* base = ring.template box<double>(seq, 0) + a.xoff;
 #pragma unroll
     for (int q = 0; q < kConvIters; ++q) {
-        const int n = tid + q * kNT;
+        const int n = conv_item(tid, q);
         if ((q + 1) * kNT <= 3 * kBoxItems || n < 3 * kBoxItems) {
             const double* src = base + cp.off[q];
             const pf p0 = split_double(src[0]), p1 = split_double(src[kHalf]);
             dst[n] = make_float4(p0.h, p1.h, p0.l, p1.l);
         }
     }
-    if (tid < 4) {
+    const int cn = tid - 32 * kCoefWarp;
+    if ((unsigned)cn < 4u) {
         const pf p = split_double(coef);
-        ps.coef[(slot % kPL) * 4 + tid] = make_float4(p.h, p.h, p.l, p.l);
+        ps.coef[(slot % kPL) * 4 + cn] = make_float4(p.h, p.h, p.l, p.l);
     }
 }
 
