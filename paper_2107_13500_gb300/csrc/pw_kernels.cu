@@ -213,63 +213,112 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 }
 
 // ---------------------------------------------------------------------------
-// Per-level mean and float perturbation. A cluster of kSplitCluster CTAs
-// takes one level: each CTA sums its share of the interior rows in FP64
-// (each thread a fixed strided subset, then a fixed-shape tree), the CTAs
-// add the cluster's partial sums in rank order through distributed shared
-// memory, and each then writes the perturbations of its share of the rows
-// (halo included). The result does not depend on scheduling.
+// Per-level mean and float perturbation, in two launches.
+//
+// split_mean_kernel: a cluster of kSplitCluster CTAs takes one level. Each
+// CTA sums its share of the interior rows in FP64 (each thread a fixed set of
+// columns, rows in order; then a fixed shuffle tree per warp and the warps in
+// order), and rank 0 adds the cluster's partial sums in rank order through
+// distributed shared memory. The result does not depend on scheduling.
+//
+// split_pert_kernel: a flat grid over every cell (halo included) writes
+// float(f - mean[k]).
+//
+// A single launch that kept each level's clusters on it for both passes was
+// slower: with one cluster per level resident at a time the grid is too small
+// to load every SM's FP64 pipe, and with all levels resident the second pass
+// re-reads the field from HBM anyway. Both kernels are bound by the FP64
+// pipe (one add per cell each).
 
-constexpr int kSplitThreads = 512, kSplitCluster = 8;
+constexpr int kSplitThreads = 256, kSplitCluster = 8, kSplitUnroll = 8;
+constexpr int kPertThreads = 128, kPertRows = 8;  // columns per CTA, rows per thread
 
 __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitThreads)
-    split_field_kernel(const double* __restrict__ f, long long fsy, long long fsz, float* __restrict__ fp,
-                       long long psy, long long psz, int nx, int ny, double* __restrict__ mean) {
-    __shared__ double part[kSplitThreads];
+    split_mean_kernel(const double* __restrict__ f, long long fsy, long long fsz, int nx, int ny, int nz,
+                      double* __restrict__ mean) {
+    __shared__ double warp_part[kSplitThreads / 32];
     __shared__ double cta_sum;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int tid = threadIdx.x;
-    const int k = blockIdx.y;
-    const double* lev = f + (size_t)k * (size_t)fsz;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // interior rows [r0, r1) of this CTA
     const int r0 = 1 + (int)((long long)ny * rank / kSplitCluster);
     const int r1 = 1 + (int)((long long)ny * (rank + 1) / kSplitCluster);
-    double s = 0.0;
-    for (int j = r0; j < r1; ++j) {
-        const double* row = lev + (size_t)j * (size_t)fsy;
-        for (int i = 1 + tid; i <= nx; i += kSplitThreads) s += row[i];
-    }
-    part[tid] = s;
-    __syncthreads();
-    for (int h = kSplitThreads / 2; h > 0; h >>= 1) {
-        if (tid < h) part[tid] += part[tid + h];
+    // the whole cluster walks the same levels
+    for (int k = blockIdx.y; k < nz; k += gridDim.y) {
+        const double* lev = f + (size_t)k * (size_t)fsz;
+        double s = 0.0;
+        for (int i = 1 + tid; i <= nx; i += kSplitThreads) {
+            const double* col = lev + i;
+            int j = r0;
+            for (; j + kSplitUnroll <= r1; j += kSplitUnroll) {
+                double x[kSplitUnroll];
+#pragma unroll
+                for (int q = 0; q < kSplitUnroll; ++q) x[q] = __ldg(col + (size_t)(j + q) * (size_t)fsy);
+#pragma unroll
+                for (int q = 0; q < kSplitUnroll; ++q) s += x[q];
+            }
+            for (; j < r1; ++j) s += __ldg(col + (size_t)j * (size_t)fsy);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) warp_part[warp] = s;
         __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kSplitThreads / 32; ++q) t += warp_part[q];
+            cta_sum = t;
+        }
+        cluster.sync();  // every CTA's partial sum is in place
+        if (rank == 0 && tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < kSplitCluster; ++q) t += *cluster.map_shared_rank(&cta_sum, q);
+            mean[k] = t / ((double)nx * (double)ny);
+        }
+        // rank 0 has read every partial sum before any CTA rewrites its own
+        // (next level) or leaves
+        cluster.sync();
     }
-    if (tid == 0) cta_sum = part[0];
-    cluster.sync();  // every CTA's partial sum is in place
-    if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < kSplitCluster; ++q) t += *cluster.map_shared_rank(&cta_sum, q);
-        part[0] = t / ((double)nx * (double)ny);
-    }
-    __syncthreads();
-    const double m = part[0];
-    cluster.sync();  // no CTA leaves while another still reads its partial sum
-    if (rank == 0 && tid == 0) mean[k] = m;
-    float* out = fp + (size_t)k * (size_t)psz;
-    const int h0 = (int)((long long)(ny + 2) * rank / kSplitCluster);
-    const int h1 = (int)((long long)(ny + 2) * (rank + 1) / kSplitCluster);
-    for (int j = h0; j < h1; ++j) {
-        const double* row = lev + (size_t)j * (size_t)fsy;
-        float* orow = out + (size_t)j * (size_t)psy;
-        for (int i = tid; i < nx + 2; i += kSplitThreads) orow[i] = (float)(row[i] - m);
+}
+
+// Thread x of CTA (bx, by, bz) converts column bx*kPertThreads + x of the
+// row chunks by, by + gridDim.y, ... (kPertRows rows each) of levels bz,
+// bz + gridDim.z, ...
+__global__ void __launch_bounds__(kPertThreads)
+    split_pert_kernel(const double* __restrict__ f, long long fsy, long long fsz, float* __restrict__ fp,
+                      long long psy, long long psz, int nx, int ny, int nz, const double* __restrict__ mean) {
+    const int i = blockIdx.x * kPertThreads + threadIdx.x;
+    if (i > nx + 1) return;
+    for (int k = blockIdx.z; k < nz; k += gridDim.z) {
+        const double m = __ldg(mean + k);
+        for (int j0 = blockIdx.y * kPertRows; j0 < ny + 2; j0 += gridDim.y * kPertRows) {
+            const double* col = f + (size_t)k * (size_t)fsz + (size_t)j0 * (size_t)fsy + i;
+            float* ocol = fp + (size_t)k * (size_t)psz + (size_t)j0 * (size_t)psy + i;
+            const int nr = min(kPertRows, ny + 2 - j0);
+            if (nr == kPertRows) {
+                double x[kPertRows];
+#pragma unroll
+                for (int q = 0; q < kPertRows; ++q) x[q] = __ldg(col + (size_t)q * (size_t)fsy);
+#pragma unroll
+                for (int q = 0; q < kPertRows; ++q) ocol[(size_t)q * (size_t)psy] = (float)(x[q] - m);
+            } else {
+                for (int q = 0; q < nr; ++q)
+                    ocol[(size_t)q * (size_t)psy] = (float)(__ldg(col + (size_t)q * (size_t)fsy) - m);
+            }
+        }
     }
 }
 
 cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, float* fp, long long psy,
                                long long psz, int nx, int ny, int nz, double* mean, cudaStream_t st) {
-    split_field_kernel<<<dim3(kSplitCluster, nz), kSplitThreads, 0, st>>>(f, fsy, fsz, fp, psy, psz, nx, ny, mean);
+    const unsigned gz = (unsigned)(nz < 65535 ? nz : 65535);  // grid y/z limit; the kernels loop over levels
+    split_mean_kernel<<<dim3(kSplitCluster, gz), kSplitThreads, 0, st>>>(f, fsy, fsz, nx, ny, nz, mean);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int chunks = (ny + 2 + kPertRows - 1) / kPertRows;
+    const dim3 grid((unsigned)((nx + 2 + kPertThreads - 1) / kPertThreads), (unsigned)(chunks < 65535 ? chunks : 65535),
+                    gz);
+    split_pert_kernel<<<grid, kPertThreads, 0, st>>>(f, fsy, fsz, fp, psy, psz, nx, ny, nz, mean);
     return cudaGetLastError();
 }
 

@@ -139,6 +139,34 @@ def test_split_field_means_and_perturbations(gpu):
     assert np.all(np.abs(p - exact) <= 2.0 ** -24 * np.abs(exact) + 1e-30)
 
 
+@pytest.mark.parametrize("nz", [5, 40])
+def test_split_field_conversion_is_the_hardware_rounding(gpu, nz):
+    """The perturbations equal the GPU's own double->float conversion of
+    f - mean[k] bit for bit (round to nearest even). Level 0 has a zero
+    interior, so its mean is exactly 0 and its halo cells reach the edge
+    cases: float overflow, infinities, NaN, float subnormals and values that
+    round to zero or to the smallest normal."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny = 77, 21
+    rng = np.random.default_rng(5)
+    u = np.zeros((nz, ny + 2, nx + 2))
+    u[1:] = rng.uniform(-10, 10, (nz - 1, ny + 2, nx + 2)) * 10.0 ** rng.integers(-3, 4, (nz - 1, ny + 2, nx + 2))
+    special = [1e39, -1e39, 3.4028235677973366e38 * (1 + 2 ** -25), np.inf, -np.inf, np.nan, 1e-40, -3e-39,
+               1e-46, 2.0 ** -126 * (1 - 2 ** -30), 2.0 ** -150, -2.0 ** -149 * 1.5, 2.0 ** -126, 0.0, -0.0]
+    u[0, 0, :len(special)] = special
+    u[0, ny + 1, :len(special)] = [-x for x in special]
+    t = to_device(u, nx, torch.float64)
+    fp, mean = pw.split_field(t, nx, ny)
+    torch.cuda.synchronize()
+    assert float(mean[0]) == 0.0
+    want = (t - mean[:, None, None]).float()[:, :, : nx + 2]
+    got = fp[:, :, : nx + 2]
+    nan = torch.isnan(want)
+    assert torch.equal(torch.isnan(got), nan)
+    assert torch.equal(got.view(torch.int32)[~nan], want.view(torch.int32)[~nan])
+
+
 @pytest.mark.parametrize("which", ["16m_modes", "134m_iid"])
 def test_split_full_size(gpu, oracle_lib, which):
     """Full-size workloads in the benchmark's launch configuration; reports
