@@ -30,13 +30,6 @@ namespace {
 
 constexpr int kTX = 32, kTY = 8, kS = 4, kFields = 6;
 
-// v where b holds, else 0 (a select, so garbage in unused halo cotangents,
-// NaN included, never reaches a result)
-template <typename T>
-__device__ __forceinline__ T gate(bool b, T v) {
-    return b ? v : T(0);
-}
-
 template <typename T>
 struct AdjShape {
     static constexpr int NT = kTX * kTY;
@@ -96,7 +89,7 @@ __device__ __forceinline__ double level_coef(const AdjArgs& a, int k, int n) {
     switch (n) {
         case 0: return (k + 1 <= nz - 1) ? __ldg(a.tzc1 + k + 1) : 0.0;  // tz1p
         case 1: return (k >= 1) ? __ldg(a.tzc2 + k - 1) : 0.0;           // tz2m
-        case 2: return __ldg(a.tzc2 + k);                                // tz20
+        case 2: return (k <= nz - 2) ? __ldg(a.tzc2 + k) : 0.0;         // tz20 (level k has an upper flux)
         case 3: return (k + 1 <= nz - 1) ? __ldg(a.tzd1 + k + 1) : 0.0;  // td1p
         case 4: return __ldg(a.tzd1 + k);                                // td10
         case 5: return (k >= 1) ? __ldg(a.tzd2 + k - 1) : 0.0;           // td2m
@@ -107,6 +100,42 @@ __device__ __forceinline__ double level_coef(const AdjArgs& a, int k, int n) {
 template <typename T>
 __device__ __forceinline__ void level_coefs(const AdjArgs& a, int k, int tid, T* dst) {
     if (tid < 7) dst[tid] = (T)level_coef(a, k, tid);
+}
+
+// Zero, in the staged cotangent boxes (gsu, gsv, gsw) of stage `slot`
+// (level lev), every cell that is not a computed output point of the forward
+// map: cells outside i = 1..nx, j = 1..ny, and whole boxes of levels where
+// the field is not computed (su, sv: levels 1..nz-1; sw: 1..nz-2). The
+// gather then needs no masks, and garbage (NaN included) in unused halo
+// cotangents never reaches a result. Only tiles at the domain edge and the
+// bottom and top levels have such cells. The writing threads order their
+// writes before the stage's next TMA load (fence.proxy.async).
+template <typename T>
+__device__ __forceinline__ void zero_outside(const AdjRing<T>& ring, int slot, int lev, const AdjArgs& a, int x0,
+                                             int y0, int tid) {
+    using Sh = AdjShape<T>;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const bool lev_s = lev >= 1 && lev <= nz - 1;
+    const bool lev_w = lev >= 1 && lev <= nz - 2;
+    // box column b holds cell i = i0 + b, box row r holds j = j0 + r
+    const int i0 = x0 - Sh::UNIT - a.xoff, j0 = y0 - 1;
+    const bool edge = i0 < 1 || i0 + Sh::BX - 1 > nx || j0 < 1 || j0 + Sh::BY - 1 > ny;
+    if (!edge && lev_s && lev_w) return;  // CTA-uniform
+    bool wrote = false;
+    for (int f = 3; f < kFields; ++f) {
+        const bool lv = (f == 5) ? lev_w : lev_s;
+        if (lv && !edge) continue;
+        T* box = const_cast<T*>(ring.box(slot, f));
+        for (int n = tid; n < Sh::BX * Sh::BY; n += kTX * kTY) {
+            const int r = n / Sh::BX, b = n - r * Sh::BX;
+            const int i = i0 + b, j = j0 + r;
+            if (!lv || i < 1 || i > nx || j < 1 || j > ny) {
+                box[n] = T(0);
+                wrote = true;
+            }
+        }
+    }
+    if (wrote) fence_proxy_async_smem();
 }
 
 template <typename T>
@@ -142,13 +171,6 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
 
     // shared index of cell (i, j): tensor x = i + xoff, box starts at bxs
     const int c0 = (ty + 1) * BX + (tx + Sh::UNIT + a.xoff);
-    // interior masks of the neighbouring output points
-    const bool mxm = (i - 1 >= 1 && i - 1 <= nx);
-    const bool mx0 = (i >= 1 && i <= nx);
-    const bool mxp = (i + 1 >= 1 && i + 1 <= nx);
-    const bool mym = (j - 1 >= 1 && j - 1 <= ny);
-    const bool my0 = (j >= 1 && j <= ny);
-    const bool myp = (j + 1 >= 1 && j + 1 <= ny);
     const T tcx = (T)a.tcx, tcy = (T)a.tcy;
     T* __restrict__ gu = static_cast<T*>(a.gu);
     T* __restrict__ gv = static_cast<T*>(a.gv);
@@ -156,7 +178,13 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
     size_t g = (size_t)j * (size_t)a.sy + (size_t)i + (size_t)kb * (size_t)a.sz;
 
     bool bad = false;
-    for (int s = 0; s < 3 && s < nseq; ++s) bad |= !ring.wait(s);  // levels kb-1, kb, kb+1
+    // levels kb-1, kb, kb+1: each staged level's cotangents are cleaned
+    // (zero_outside) one step before the step that first reads it
+    for (int s = 0; s < 3 && s < nseq; ++s) {
+        const bool ok = ring.wait(s);
+        bad |= !ok;
+        if (ok) zero_outside(ring, s % kS, kb - 1 + s, a, x0, y0, tid);
+    }
     level_coefs<T>(a, kb, tid, coef_s[0]);
     bool abort = __syncthreads_or(bad);
 
@@ -164,7 +192,11 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
         const int r = k - kb;
         // next level's coefficient, loaded now so that its latency is hidden by the step
         const double c_next = (tid < 7 && k + 1 < ke) ? level_coef(a, k + 1, tid) : 0.0;
-        if (r > 0) bad |= !ring.wait(r + 2);  // level k+1 (load r+2)
+        if (r + 3 < nseq) {  // level k+2 (load r+3), read from the next step on
+            const bool ok = ring.wait(r + 3);
+            bad |= !ok;
+            if (ok) zero_outside(ring, (r + 3) % kS, k + 2, a, x0, y0, tid);
+        }
         // stages of levels k-1, k, k+1
         const int sm = r % kS, s0 = (r + 1) % kS, sp = (r + 2) % kS;
         const T* Um = ring.box(sm, 0);
@@ -185,50 +217,22 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
         const T* GWm = ring.box(sm, 5);
         const T* GW0 = ring.box(s0, 5);
         const T* GWp = ring.box(sp, 5);
-        // level masks: su, sv computed on levels 1..nz-1; sw on 1..nz-2
-        const bool l_m = (k - 1 >= 1);
-        const bool l_0 = (k >= 1);
-        const bool l_p = (k + 1 <= nz - 1);
-        const bool w_m = (k - 1 >= 1 && k - 1 <= nz - 2);
-        const bool w_0 = (k >= 1 && k <= nz - 2);
-        const bool w_p = (k + 1 <= nz - 2);
-        const bool up0 = (k <= nz - 2);  // level k has an upper flux
         const T* cs = coef_s[r & 1];
         const T tz1p = cs[0], tz2m = cs[1], tz20 = cs[2], td1p = cs[3], td10 = cs[4], td2m = cs[5], td20 = cs[6];
         constexpr int E = 1, N = BX;
 
-        // masked cotangents (index: P = C + offset)
-        const T su_c = gate(mx0 && my0 && l_0, GU0[c0]);
-        const T su_e = gate(mxp && my0 && l_0, GU0[c0 + E]);
-        const T su_w = gate(mxm && my0 && l_0, GU0[c0 - E]);
-        const T su_n = gate(mx0 && myp && l_0, GU0[c0 + N]);
-        const T su_s = gate(mx0 && mym && l_0, GU0[c0 - N]);
-        const T su_nw = gate(mxm && myp && l_0, GU0[c0 + N - E]);
-        const T su_w_up = gate(mxm && my0 && l_0 && up0, GU0[c0 - E]);
-        const T su_c_up = gate(up0, su_c);
-        const T su_km = gate(mx0 && my0 && l_m, GUm[c0]);
-        const T su_kp = gate(mx0 && my0 && l_p, GUp[c0]);
-        const T su_kp_w = gate(mxm && my0 && l_p, GUp[c0 - E]);
-        const T sv_c = gate(mx0 && my0 && l_0, GV0[c0]);
-        const T sv_e = gate(mxp && my0 && l_0, GV0[c0 + E]);
-        const T sv_w = gate(mxm && my0 && l_0, GV0[c0 - E]);
-        const T sv_n = gate(mx0 && myp && l_0, GV0[c0 + N]);
-        const T sv_s = gate(mx0 && mym && l_0, GV0[c0 - N]);
-        const T sv_se = gate(mxp && mym && l_0, GV0[c0 - N + E]);
-        const T sv_s_up = gate(up0, sv_s);
-        const T sv_c_up = gate(up0, sv_c);
-        const T sv_km = gate(mx0 && my0 && l_m, GVm[c0]);
-        const T sv_kp = gate(mx0 && my0 && l_p, GVp[c0]);
-        const T sv_kp_s = gate(mx0 && mym && l_p, GVp[c0 - N]);
-        const T sw_c = gate(mx0 && my0 && w_0, GW0[c0]);
-        const T sw_e = gate(mxp && my0 && w_0, GW0[c0 + E]);
-        const T sw_w = gate(mxm && my0 && w_0, GW0[c0 - E]);
-        const T sw_n = gate(mx0 && myp && w_0, GW0[c0 + N]);
-        const T sw_s = gate(mx0 && mym && w_0, GW0[c0 - N]);
-        const T sw_km = gate(mx0 && my0 && w_m, GWm[c0]);
-        const T sw_km_e = gate(mxp && my0 && w_m, GWm[c0 + E]);
-        const T sw_km_n = gate(mx0 && myp && w_m, GWm[c0 + N]);
-        const T sw_kp = gate(mx0 && my0 && w_p, GWp[c0]);
+        // cotangents (index: P = C + offset); cells that are not computed
+        // points were zeroed in the stages (zero_outside), and the upper
+        // flux of the top level is absent through its coefficient (tz20 = 0)
+        const T su_c = GU0[c0], su_e = GU0[c0 + E], su_w = GU0[c0 - E], su_n = GU0[c0 + N], su_s = GU0[c0 - N];
+        const T su_nw = GU0[c0 + N - E];
+        const T su_km = GUm[c0], su_kp = GUp[c0], su_kp_w = GUp[c0 - E];
+        const T sv_c = GV0[c0], sv_e = GV0[c0 + E], sv_w = GV0[c0 - E], sv_n = GV0[c0 + N], sv_s = GV0[c0 - N];
+        const T sv_se = GV0[c0 - N + E];
+        const T sv_km = GVm[c0], sv_kp = GVp[c0], sv_kp_s = GVp[c0 - N];
+        const T sw_c = GW0[c0], sw_e = GW0[c0 + E], sw_w = GW0[c0 - E], sw_n = GW0[c0 + N], sw_s = GW0[c0 - N];
+        const T sw_km = GWm[c0], sw_km_e = GWm[c0 + E], sw_km_n = GWm[c0 + N];
+        const T sw_kp = GWp[c0];
 
         // fields around C
         const T u_c = U0[c0], u_e = U0[c0 + E], u_w = U0[c0 - E], u_n = U0[c0 + N], u_nw = U0[c0 + N - E];
@@ -257,8 +261,8 @@ __global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant
         // gw(C): T5 (P=C+z, P=C+z-x), T6 (P=C, P=C-x), S5 (P=C+z, P=C+z-y),
         // S6 (P=C, P=C-y), W1 (P=C+x), W2 (P=C-x), W3 (P=C+y), W4 (P=C-y),
         // W5 (P=C+z, P=C), W6 (P=C-z, P=C)
-        T r_w = tz1p * (u_c * su_kp + u_w * su_kp_w) - tz20 * (u_kp * su_c_up + u_kp_w * su_w_up);
-        r_w += tz1p * (v_c * sv_kp + v_s * sv_kp_s) - tz20 * (v_kp * sv_c_up + v_kp_s * sv_s_up);
+        T r_w = tz1p * (u_c * su_kp + u_w * su_kp_w) - tz20 * (u_kp * su_c + u_kp_w * su_w);
+        r_w += tz1p * (v_c * sv_kp + v_s * sv_kp_s) - tz20 * (v_kp * sv_c + v_kp_s * sv_s);
         r_w += tcx * ((u_c + u_kp) * sw_e - (u_w + u_kp_w) * sw_w);
         r_w += tcy * ((v_c + v_kp) * sw_n - (v_s + v_kp_s) * sw_s);
         r_w += td1p * (w_kp + w_c + w_c) * sw_kp + td10 * w_kmc * sw_c;
