@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 namespace pw {
 
@@ -121,6 +124,132 @@ cudaError_t choose_kchunks(Kern kern, int threads, int smem, long long tiles, in
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
     *chunks = pick_kchunks(tiles, nz, (long long)sms * (per_sm > 0 ? per_sm : 1));
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------- one-shot schedule
+// Work items of a one-shot forward launch (a 1-D grid, one CTA per item). A
+// tile column is one tile of the x-y grid over the computed levels
+// kbeg..kend-1. Tiles [0, ta) are cut into ca level chunks and come first;
+// tiles [ta, tiles) are cut into cb chunks. Chunks re-read one level below
+// and one above, so whole columns are cheapest; chunks make enough small
+// items for the last wave of CTAs. The block scheduler starts CTAs in
+// index order, so the short items of the second group fill the tail.
+// Within a group items run chunk by chunk (every tile's first chunk, then
+// every tile's second, ...), so CTAs in flight together read the same
+// levels of neighbouring tiles.
+struct ItemSched {
+    int tiles_x;         // tiles per row of the tile grid
+    int ta, ca, cb;      // tiles of the first group; chunks per tile in each group
+    long long items_a;   // ta * ca
+    long long items;     // all items (grid size)
+};
+
+// Tile and relative level range [k0, k1) (0 <= k0 < k1 <= nlev) of item b.
+__host__ __device__ __forceinline__ void sched_item(const ItemSched& s, int nlev, long long b, int* bx, int* by,
+                                                    int* k0, int* k1) {
+    long long t;
+    int ch, c;
+    if (b < s.items_a) {
+        ch = (int)(b / s.ta);
+        t = b - (long long)ch * s.ta;
+        c = s.ca;
+    } else {
+        const long long r = b - s.items_a;
+        const long long nb = (s.items - s.items_a) / s.cb;  // tiles of the second group (>= 1 here)
+        ch = (int)(r / nb);
+        t = s.ta + (r - (long long)ch * nb);
+        c = s.cb;
+    }
+    *bx = (int)(t % s.tiles_x);
+    *by = (int)(t / s.tiles_x);
+    *k0 = (int)((long long)nlev * ch / c);
+    *k1 = (int)((long long)nlev * (ch + 1) / c);
+}
+
+// Makespan of greedy list scheduling (each item to the least-loaded slot, in
+// order) of na items of length la, then nb items of length lb, on `slots`
+// equal slots. Slots with equal loads are kept as one entry with a count.
+inline double greedy_makespan(long long na, double la, long long nb, double lb, long long slots) {
+    std::map<double, long long> load;
+    load[0.0] = slots;
+    auto place = [&load](long long n, double len) {
+        while (n > 0) {
+            auto it = load.begin();
+            const double l = it->first;
+            const long long k = it->second < n ? it->second : n;
+            if (k == it->second) load.erase(it);
+            else it->second -= k;
+            load[l + len] += k;
+            n -= k;
+        }
+    };
+    place(na, la);
+    place(nb, lb);
+    return load.rbegin()->first;
+}
+
+// Items of one launch: a uniform cut (every tile in c chunks, as
+// pick_kchunks allows) or whole waves of tiles in ca = 1 or 2 chunks followed
+// by the remaining tiles in finer chunks (at least 4 levels each), whichever
+// the greedy model finishes first. An item of L levels costs L + kItemCost
+// level-times (its two re-read levels and its pipeline start); 1, 2 and 4
+// were measured, and 1 was fastest by about 0.5 % on every kernel.
+inline ItemSched pick_sched(long long tiles, int tiles_x, int nlev, long long slots) {
+#ifndef PW_ITEM_COST
+#define PW_ITEM_COST 1.0
+#endif
+    constexpr double kItemCost = PW_ITEM_COST;
+    const bool small = tiles * 8 < slots;
+    const int max_chunks = small ? 64 : 8, min_levels = small ? 2 : 8;
+    ItemSched best{tiles_x, (int)tiles, 1, 1, tiles, tiles};
+    double best_t = greedy_makespan(tiles, nlev + kItemCost, 0, 0.0, slots);
+    for (int c = 2; c <= max_chunks && nlev / c >= min_levels; ++c) {
+        const double t = greedy_makespan(tiles * c, (double)nlev / c + kItemCost, 0, 0.0, slots);
+        if (t < best_t - 1e-9) {
+            best_t = t;
+            best = ItemSched{tiles_x, (int)tiles, c, 1, tiles * c, tiles * c};
+        }
+    }
+    if (!small) {
+        for (int ca = 1; ca <= 2 && (ca == 1 || nlev / ca >= min_levels); ++ca) {
+            const long long waves = tiles * ca / slots;
+            if (waves < 1) continue;
+            const long long ta = waves * slots / ca;
+            if (ta >= tiles) continue;
+            for (int cb = ca + 1; cb <= 64 && nlev / cb >= 4; ++cb) {
+                const double t = greedy_makespan(ta * ca, (double)nlev / ca + kItemCost, (tiles - ta) * cb,
+                                                 (double)nlev / cb + kItemCost, slots);
+                if (t < best_t - 1e-9) {
+                    best_t = t;
+                    best = ItemSched{tiles_x, (int)ta, ca, cb, ta * ca, ta * ca + (tiles - ta) * cb};
+                }
+            }
+        }
+    }
+    return best;
+}
+
+// The schedule of a one-shot launch of `kern`, cached per shape (the search
+// runs once per tile count, level count and occupancy).
+template <typename Kern>
+cudaError_t choose_sched(Kern kern, int threads, int smem, int tiles_x, int tiles_y, int nlev, ItemSched* out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem)) != cudaSuccess) return e;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, long long>, ItemSched> cache;
+    const auto key = std::make_tuple(tiles_x, tiles_y, nlev, slots);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it == cache.end()) {
+        if (cache.size() > 4096) cache.clear();
+        it = cache.emplace(key, pick_sched((long long)tiles_x * tiles_y, tiles_x, nlev, slots)).first;
+    }
+    *out = it->second;
     return cudaSuccess;
 }
 

@@ -25,14 +25,14 @@ namespace cg = cooperative_groups;
 constexpr int kF64TX = 32, kF64TY = 8, kF64S = 4;
 using F64Shape = RingShape<double, kF64TX, kF64TY, kF64S>;
 
-// One CTA: a 32x8 tile of columns, output levels kb..ke-1 of its k-chunk
-// (blockIdx.z splits kbeg..kend-1); it reads levels lo = max(kb-1, 0) ..
-// hi = min(ke, nz-1). Loads are numbered relative to lo.
+// One CTA: work item blockIdx.x of the schedule, a 32x8 tile of columns and
+// output levels kb..ke-1 (a chunk of kbeg..kend-1); it reads levels
+// lo = max(kb-1, 0) .. hi = min(ke, nz-1). Loads are numbered relative to lo.
 template <typename Shape>
 __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constant__ CUtensorMap mu,
                                                             const __grid_constant__ CUtensorMap mv,
                                                             const __grid_constant__ CUtensorMap mw,
-                                                            const FwdArgs a) {
+                                                            const FwdArgs a, const ItemSched sched) {
     constexpr int TX = Shape::TX, TY = Shape::TY, S = Shape::S, BX = Shape::BX;
     extern __shared__ unsigned char smem_raw[];
     Ring<Shape> ring;
@@ -40,12 +40,14 @@ __global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constan
 
     const int tid = threadIdx.x;
     const int tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    int bx, by, kb, ke;
+    sched_item(sched, a.kend - a.kbeg, blockIdx.x, &bx, &by, &kb, &ke);
+    kb += a.kbeg;
+    ke += a.kbeg;
+    const int x0 = bx * TX, y0 = by * TY;
     const int i = x0 + 1 + tx, j = y0 + 1 + ty;
     const bool act = (i <= a.nx) && (j <= a.ny);
     const int nz = a.nz;
-    const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
-    const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
     const int lo = kb > 0 ? kb - 1 : 0, hi = ke < nz ? ke : nz - 1;
     const int nl = hi - lo + 1;  // levels read
 
@@ -165,12 +167,11 @@ cudaError_t launch_fwd_f64(const CUtensorMap& mu, const CUtensorMap& mv, const C
     auto kern = fwd_f64_kernel<F64Shape>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F64Shape::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)((a.nx + kF64TX - 1) / kF64TX) * ((a.ny + kF64TY - 1) / kF64TY);
-    int chunks = 1;
-    if ((e = choose_kchunks(kern, F64Shape::NT, F64Shape::SMEM_BYTES, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess)
+    ItemSched sched;
+    if ((e = choose_sched(kern, F64Shape::NT, F64Shape::SMEM_BYTES, (a.nx + kF64TX - 1) / kF64TX,
+                          (a.ny + kF64TY - 1) / kF64TY, a.kend - a.kbeg, &sched)) != cudaSuccess)
         return e;
-    dim3 grid((a.nx + kF64TX - 1) / kF64TX, (a.ny + kF64TY - 1) / kF64TY, chunks);
-    kern<<<grid, F64Shape::NT, F64Shape::SMEM_BYTES, st>>>(mu, mv, mw, a);
+    kern<<<(unsigned)sched.items, F64Shape::NT, F64Shape::SMEM_BYTES, st>>>(mu, mv, mw, a, sched);
     return cudaGetLastError();
 }
 

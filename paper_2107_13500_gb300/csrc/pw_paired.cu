@@ -345,7 +345,7 @@ template <class C>
 __global__ void __launch_bounds__(C::kNT, C::kMinBlocks) fwd_paired_kernel(const __grid_constant__ CUtensorMap mu,
                                                                            const __grid_constant__ CUtensorMap mv,
                                                                            const __grid_constant__ CUtensorMap mw,
-                                                                           const FwdArgs a) {
+                                                                           const FwdArgs a, const ItemSched sched) {
     using K = PairedK<C>;
     extern __shared__ unsigned char smem_raw[];
     Ring<typename C::Shape> ring;
@@ -360,10 +360,10 @@ __global__ void __launch_bounds__(C::kNT, C::kMinBlocks) fwd_paired_kernel(const
     }
     __syncthreads();
     long long seq = 0;
-    const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
-    const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
+    int bx, by, k0, k1;
+    sched_item(sched, a.kend - a.kbeg, blockIdx.x, &bx, &by, &k0, &k1);
     const typename K::ConvPlan cp = K::make_conv_plan(tid);
-    (void)K::paired_tile(ring, ps, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid, cp);
+    (void)K::paired_tile(ring, ps, &mu, &mv, &mw, a, bx, by, a.kbeg + k0, a.kbeg + k1, seq, tid, cp);
 }
 
 // Persistent form over a batch plan: work items (one tile of one domain)
@@ -416,11 +416,11 @@ cudaError_t launch_one(const CUtensorMap& mu, const CUtensorMap& mv, const CUten
     auto kern = fwd_paired_kernel<C>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmemBytes);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)((a.nx + C::kTX - 1) / C::kTX) * ((a.ny + C::kTY - 1) / C::kTY);
-    int chunks = 1;
-    if ((e = choose_kchunks(kern, C::kNT, C::kSmemBytes, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess) return e;
-    dim3 grid((a.nx + C::kTX - 1) / C::kTX, (a.ny + C::kTY - 1) / C::kTY, chunks);
-    kern<<<grid, C::kNT, C::kSmemBytes, st>>>(mu, mv, mw, a);
+    ItemSched sched;
+    if ((e = choose_sched(kern, C::kNT, C::kSmemBytes, (a.nx + C::kTX - 1) / C::kTX, (a.ny + C::kTY - 1) / C::kTY,
+                          a.kend - a.kbeg, &sched)) != cudaSuccess)
+        return e;
+    kern<<<(unsigned)sched.items, C::kNT, C::kSmemBytes, st>>>(mu, mv, mw, a, sched);
     return cudaGetLastError();
 }
 

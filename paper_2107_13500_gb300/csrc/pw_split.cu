@@ -312,7 +312,7 @@ template <class Cfg, bool kVec>
 __global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS) fwd_split_kernel(const __grid_constant__ CUtensorMap mu,
                                                             const __grid_constant__ CUtensorMap mv,
                                                             const __grid_constant__ CUtensorMap mw,
-                                                            const FwdArgs a) {
+                                                            const FwdArgs a, const ItemSched sched) {
     extern __shared__ unsigned char smem_raw[];
     SplitRing<Cfg> ring;
     ring.setup(smem_raw);
@@ -325,9 +325,9 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS) fwd_split_kernel(con
     }
     __syncthreads();
     long long seq = 0;
-    const int kb = a.kbeg + (int)((long long)(a.kend - a.kbeg) * blockIdx.z / gridDim.z);
-    const int ke = a.kbeg + (int)((long long)(a.kend - a.kbeg) * (blockIdx.z + 1) / gridDim.z);
-    (void)split_tile<Cfg, kVec>(ring, &mu, &mv, &mw, a, blockIdx.x, blockIdx.y, kb, ke, seq, tid);
+    int bx, by, k0, k1;
+    sched_item(sched, a.kend - a.kbeg, blockIdx.x, &bx, &by, &k0, &k1);
+    (void)split_tile<Cfg, kVec>(ring, &mu, &mv, &mw, a, bx, by, a.kbeg + k0, a.kbeg + k1, seq, tid);
 }
 
 // Persistent form: the CTA takes work items (one k-chunk of one tile of one
@@ -396,11 +396,11 @@ cudaError_t launch_one(const CUtensorMap& mu, const CUtensorMap& mv, const CUten
     auto kern = a.vec ? fwd_split_kernel<Cfg, true> : fwd_split_kernel<Cfg, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)((a.nx + Cfg::TXP - 1) / Cfg::TXP) * ((a.ny + Cfg::TY - 1) / Cfg::TY);
-    int chunks = 1;
-    if ((e = choose_kchunks(kern, Cfg::NT, Cfg::SMEM_BYTES, tiles, a.kend - a.kbeg, &chunks)) != cudaSuccess) return e;
-    dim3 grid((a.nx + Cfg::TXP - 1) / Cfg::TXP, (a.ny + Cfg::TY - 1) / Cfg::TY, chunks);
-    kern<<<grid, Cfg::NT, Cfg::SMEM_BYTES, st>>>(mu, mv, mw, a);
+    ItemSched sched;
+    if ((e = choose_sched(kern, Cfg::NT, Cfg::SMEM_BYTES, (a.nx + Cfg::TXP - 1) / Cfg::TXP, (a.ny + Cfg::TY - 1) / Cfg::TY,
+                          a.kend - a.kbeg, &sched)) != cudaSuccess)
+        return e;
+    kern<<<(unsigned)sched.items, Cfg::NT, Cfg::SMEM_BYTES, st>>>(mu, mv, mw, a, sched);
     return cudaGetLastError();
 }
 
