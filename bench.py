@@ -45,9 +45,9 @@ METRIC = "GPoints/s of su,sv,sw (FP64-accurate, <=1e-13 of the FP64 oracle) and 
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 # Sources of each mode's forward kernel: a stored ncu traffic figure is used
 # only while the hash of these files matches the one it was captured with.
-KERNEL_SOURCES = {"paired": ["pw_paired.cu", "pw_pair.cuh", "pw_ring.cuh", "pw_common.cuh"],
-                  "split": ["pw_split.cu", "pw_ring.cuh", "pw_common.cuh"],
-                  "f64": ["pw_kernels.cu", "pw_ring.cuh", "pw_common.cuh"]}
+KERNEL_SOURCES = {"paired": ["pw_paired.cu", "pw_pair.cuh", "pw_ring.cuh", "pw_common.cuh", "pw_internal.h"],
+                  "split": ["pw_split.cu", "pw_ring.cuh", "pw_common.cuh", "pw_internal.h"],
+                  "f64": ["pw_kernels.cu", "pw_ring.cuh", "pw_common.cuh", "pw_internal.h"]}
 # Paired-FP32 algorithm, FP32/INT lane operations per point as written: 31 pair
 # sums x 8 + 28 pair products x 4 + 3 double->pair splits x 15 + 3 pair->double
 # joins x 15 (halo re-splits and address/loop work excluded).
