@@ -191,3 +191,29 @@ def test_rollout_gradient_checkpointed_and_fd(gpu):
     fd = (jp - jm) / (2 * h)
     an = sum(float((g * dd).sum()) for g, dd in zip(g_ck, d))
     assert abs(fd - an) <= 1e-6 * max(abs(an), 1.0), (fd, an)
+
+
+@pytest.mark.parametrize("mode", ["f64", "paired", "f32"])
+def test_adjoint_euler_identity(gpu, mode):
+    """Euler's identity for the quadratic map, J(x) x = 2 F(x), seen through
+    the adjoint: <J(x)^T y, x> = 2 <y, F(x)>, summed over every cell the
+    forward reads (the outputs' halo is left zero, so F vanishes off the
+    computed points). Independent of any finite-difference step."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    dt = torch.float32 if mode == "f32" else torch.float64
+    nx, ny, nz = 96, 40, 24
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    c = pw.make_coeffs(nz, 50.0, 50.0, dz, rho, rhon).to_device()
+    x = [to_device(_raw(nx, ny, nz, 71, s, -10.0, 10.0), nx, dt) for s in range(3)]
+    y = [to_device(_raw(nx, ny, nz, 72, s), nx, dt) for s in range(3)]
+    f = pw.advect(*x, c, nx, ny, mode="f32" if mode == "f32" else "f64")
+    g = pw.advect_adjoint(*x, c, nx, ny, *y, mode=mode)
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    cells = (slice(None), slice(None), slice(0, nx + 2))
+    lhs = sum(float((gg[cells].double() * xx[cells].double()).sum()) for gg, xx in zip(g, x))
+    rhs = 2.0 * sum(float((yy[cells].double() * ff[cells].double()).sum()) for yy, ff in zip(y, f))
+    scale = sum(float((gg[cells].double() * xx[cells].double()).abs().sum()) for gg, xx in zip(g, x))
+    assert abs(lhs - rhs) <= (1e-5 if mode == "f32" else 1e-12) * scale, (lhs, rhs, scale)

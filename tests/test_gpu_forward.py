@@ -270,3 +270,38 @@ def test_host_chunked_matches_device_call(gpu, mode, nchunks):
     for g, w_ in zip(got, want):
         assert torch.equal(g[:, 1:ny + 1, 1:nx + 1], w_.cpu()[:, 1:ny + 1, 1:nx + 1])
         assert float((g[:, 0, :] - 7.0).abs().sum()) == 0.0 and float((g[:, ny + 1, :] - 7.0).abs().sum()) == 0.0
+
+
+@pytest.mark.parametrize("mode", ["f64", "paired", "f32", "split"])
+def test_homogeneity_bit_exact(gpu, mode):
+    """The map is a quadratic form, so F(2x) = 4 F(x). Scaling by a power of
+    two is exact through every product, FMA, pair split and join, level mean
+    and split-table constant, so each mode must give 4 F(x) bit for bit
+    (stretched grid with density, ragged tiles, several k-chunks)."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 77, 29, 23
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    c = pw.make_coeffs(nz, 50.0, 50.0, dz, rho, rhon).to_device()
+    fields = synth.fields_modes(nx, ny, nz, 50.0, 50.0, dz, seed=13)
+
+    def evaluate(scale):
+        if mode in ("f64", "paired"):
+            x = [to_device(scale * f, nx, torch.float64) for f in fields]
+            return pw.advect(*x, c, nx, ny, mode=mode)
+        if mode == "f32":
+            x = [to_device(scale * f, nx, torch.float32) for f in fields]
+            return pw.advect(*x, c, nx, ny, mode="f32")
+        x = [to_device(scale * f, nx, torch.float64) for f in fields]
+        fp, means = zip(*(pw.split_field(t, nx, ny) for t in x))
+        table = torch.from_numpy(pw.make_split_table(c, *(m.cpu().numpy() for m in means))).cuda()
+        return pw.advect(*fp, c, nx, ny, mode="split", split_table=table)
+
+    one, two = evaluate(1.0), evaluate(2.0)
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    for a, b in zip(one, two):
+        a, b = a[:, :, : nx + 2], b[:, :, : nx + 2]
+        assert torch.isfinite(a).all()
+        assert torch.equal(4 * a, b)
