@@ -41,7 +41,6 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libpw.so")
 
 
-
 class PWError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"[{code}] {msg}")
