@@ -25,6 +25,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -43,11 +44,11 @@ WORKLOAD = ("pw_advect su,sv,sw 512x512x64 (16.8M points), FP64 in/out, smooth 8
             "+1% noise, 5 m/s mean wind, dx=dy=50 m, stretched dz=10 m*1.03^(k-2)")
 METRIC = "GPoints/s of su,sv,sw (FP64-accurate, <=1e-13 of the FP64 oracle) and % HBM roofline"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
-# Sources of each mode's forward kernel: a stored ncu traffic figure is used
-# only while the hash of these files matches the one it was captured with.
-KERNEL_SOURCES = {"paired": ["pw_paired.cu", "pw_pair.cuh", "pw_ring.cuh", "pw_common.cuh", "pw_internal.h"],
-                  "split": ["pw_split.cu", "pw_ring.cuh", "pw_common.cuh", "pw_internal.h"],
-                  "f64": ["pw_kernels.cu", "pw_ring.cuh", "pw_common.cuh", "pw_internal.h"]}
+# Translation unit of each mode's forward kernel: a stored ncu traffic figure
+# is used only while the hash of that file and of every local header it
+# includes (transitively) matches the one it was captured with.
+KERNEL_FILES = {"paired": "pw_paired.cu", "split": "pw_split.cu", "f64": "pw_kernels.cu"}
+SOURCE_DIRS = (os.path.join(ROOT, "paper_2107_13500_gb300", "csrc"), os.path.join(ROOT, "include"))
 # Paired-FP32 algorithm, FP32/INT lane operations per point as written: 31 pair
 # sums x 8 + 28 pair products x 4 + 3 double->pair splits x 15 + 3 pair->double
 # joins x 15 (halo re-splits and address/loop work excluded).
@@ -70,10 +71,27 @@ def parse_args():
 
 # ----------------------------------------------------------------------------- helpers
 
+def kernel_sources(mode):
+    """Paths of the kernel's translation unit and of every local header
+    (#include "...") it reaches, sorted by file name."""
+    found, todo = {}, [KERNEL_FILES[mode]]
+    while todo:
+        name = todo.pop()
+        if name in found:
+            continue
+        path = next((os.path.join(d, name) for d in SOURCE_DIRS if os.path.exists(os.path.join(d, name))), None)
+        if path is None:
+            continue  # a system header
+        found[name] = path
+        with open(path) as fh:
+            todo += re.findall(r'^\s*#\s*include\s+"([^"]+)"', fh.read(), flags=re.M)
+    return [found[k] for k in sorted(found)]
+
+
 def kernel_source_hash(mode):
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES[mode]:
-        with open(os.path.join(ROOT, "paper_2107_13500_gb300", "csrc", name), "rb") as fh:
+    for path in kernel_sources(mode):
+        with open(path, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
