@@ -1,5 +1,6 @@
 """Host logic of the one-shot launch schedule: the work items of a launch
-cover every (tile, level) exactly once (tests/sched_check.cpp, compiled
+cover every (tile, level) exactly once, and the grouped list-scheduling
+model matches an item-by-item simulation (tests/sched_check.cpp, compiled
 against the library's internal header with the host compiler)."""
 import os
 import shutil
