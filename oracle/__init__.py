@@ -9,5 +9,8 @@ from .oracle import (  # noqa: F401
     coeffs,
     advect,
     advect_adjoint,
+    monomial_scale,
+    energy_weights,
+    energy_budget,
     flops_per_column,
 )

@@ -52,6 +52,14 @@ def _load():
             lib.pwo_advect_adjoint.restype = None
             lib.pwo_advect_adjoint.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_longlong] * 2 + [_dp] * 3
                                                + [ctypes.c_double] * 2 + [_dp] * 4 + [_dp] * 6)
+            lib.pwo_monomial_scale.restype = None
+            lib.pwo_monomial_scale.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_longlong] * 2 + [_dp] * 3
+                                               + [ctypes.c_double] * 2 + [_dp] * 4 + [_dp] * 3 + [ctypes.c_int])
+            lib.pwo_energy_weights.restype = ctypes.c_int
+            lib.pwo_energy_weights.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+            lib.pwo_energy_budget.restype = None
+            lib.pwo_energy_budget.argtypes = ([ctypes.c_int] * 3 + [ctypes.c_longlong] * 2 + [_dp] * 6
+                                              + [_dp] * 3)
             lib.pwo_flops_per_column.restype = ctypes.c_longlong
             lib.pwo_flops_per_column.argtypes = [ctypes.c_int]
             _lib = lib
@@ -91,8 +99,10 @@ def _dims(u, nx, ny):
 def advect(u, v, w, c, nx, ny, want_abs=False, nthreads=1, out=None):
     """Source terms (su, sv, sw) [, (asu, asv, asw)] for fields u, v, w.
 
-    Outputs have the inputs' shape; only the interior is written, the halo of
-    freshly allocated outputs is zero.
+    With want_abs the second triple is the per-point error scale: the sum of
+    |c||q||a+b| over the face terms c*q*(a+b) of each output. Outputs have
+    the inputs' shape; only the interior is written, the halo of freshly
+    allocated outputs is zero.
     """
     lib = _load()
     nz, sy, sz = _dims(u, nx, ny)
@@ -109,6 +119,44 @@ def advect(u, v, w, c, nx, ny, want_abs=False, nthreads=1, out=None):
     if want_abs:
         return (su, sv, sw), tuple(ab)
     return su, sv, sw
+
+
+def monomial_scale(u, v, w, c, nx, ny, nthreads=1):
+    """Per-point monomial error scale (msu, msv, msw): each face term
+    c*q*(a+b) counted as |c||q|(|a|+|b|) (interior; halo zero)."""
+    lib = _load()
+    nz, sy, sz = _dims(u, nx, ny)
+    out = [np.zeros_like(u) for _ in range(3)]
+    lib.pwo_monomial_scale(nx, ny, nz, sy, sz, _ptr(u), _ptr(v), _ptr(w), c["tcx"], c["tcy"],
+                           _ptr(c["tzc1"]), _ptr(c["tzc2"]), _ptr(c["tzd1"]), _ptr(c["tzd2"]),
+                           _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), int(nthreads))
+    return tuple(out)
+
+
+def energy_weights(nz, dz, rho=None, rhon=None):
+    """(wu, ww): mass of the u/v cells and of the w cells per level."""
+    lib = _load()
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    rhon = None if rhon is None else np.ascontiguousarray(rhon, dtype=np.float64)
+    wu, ww = np.zeros(nz), np.zeros(nz)
+    if lib.pwo_energy_weights(nz, _ptr(dz), _ptr(rho), _ptr(rhon), _ptr(wu), _ptr(ww)) != 0:
+        raise ValueError("pwo_energy_weights: bad arguments")
+    return wu, ww
+
+
+def energy_budget(u, v, w, su, sv, sw, wu, ww, nx, ny):
+    """[sum wu u su, sum wu v sv, sum ww w sw, and the three sums of the
+    absolute summands] over the interior."""
+    lib = _load()
+    nz, sy, sz = _dims(u, nx, ny)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (u, v, w, su, sv, sw)]
+    for a in arrs:
+        assert a.shape == u.shape
+    out = np.zeros(6)
+    lib.pwo_energy_budget(nx, ny, nz, sy, sz, *[_ptr(a) for a in arrs], _ptr(np.ascontiguousarray(wu)),
+                          _ptr(np.ascontiguousarray(ww)), _ptr(out))
+    return out
 
 
 def advect_adjoint(u, v, w, c, nx, ny, gsu, gsv, gsw):

@@ -8,14 +8,19 @@
  *
  * What it follows (paper: N. Brown, "Accelerating advection for atmospheric
  * modelling on Xilinx and Intel FPGAs", arXiv:2107.13500):
- *   - su: Listing 1 of Sec. II-A, term by term and in its evaluation order,
- *     over k = 2..nz with the upper vertical flux dropped at k = nz.
- *   - sv, sw: Sec. II-A says the scheme loops over U, V and W and returns the
- *     three source terms, 21 operations each (Sec. III), but prints only su.
- *     sv is su with the roles of x and y (u and v, tcx and tcy) exchanged;
- *     sw applies the same flux form to w on its own (w-level) grid. Both are
- *     readings, pinned by the tests (transpose identity, energy conservation,
- *     second-order convergence, closed forms).
+ *   - Sec. II-A: the PW scheme returns the source terms su, sv, sw of the
+ *     three wind fields in flux form; Listing 1 prints su. Each term is
+ *     computed here per direction as inflow through the lower face minus
+ *     outflow through the upper face, a flux being the neighbour's value
+ *     times the sum of the two velocity samples at the face, weighted by
+ *     tcx, tcy or the vertical coefficients (see `gather` below), over
+ *     k = 2..nz with the upper vertical face dropped at k = nz.
+ *   - sv, sw: Sec. II-A says the scheme returns all three source terms, 21
+ *     operations each (Sec. III), but prints only su. sv is su with the
+ *     roles of x and y (u and v, tcx and tcy) exchanged; sw applies the same
+ *     flux form to w on its own (w-level) grid. Both are readings, pinned by
+ *     the tests (transpose identity, energy conservation, second-order
+ *     convergence, closed forms).
  *   - Staggering (Arakawa C): u at (i+1/2, j, zn_k), v at (i, j+1/2, zn_k),
  *     w at (i, j, z_k), the top face of cell k.
  *   - Level 1 is not computed (Listing 1 starts at k = 2): outputs there are
@@ -95,13 +100,121 @@ int pwo_coeffs(int nz, double dx, double dy, const double *dz,
     return 0;
 }
 
-void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
-                const double *u, const double *v, const double *w,
-                double tcx, double tcy,
-                const double *tzc1, const double *tzc2,
-                const double *tzd1, const double *tzd2,
-                double *su, double *sv, double *sw,
-                double *asu, double *asv, double *asw, int nthreads)
+/*
+ * Forward map, written per face. Sec. II-A computes each source term in the
+ * flux form of the Piacsek-Williams scheme: for every direction, what enters
+ * through the lower face minus what leaves through the upper face. The
+ * "flux" through a face is the advected field's value at the neighbour
+ * across that face, q, times the sum a + b of the two velocity samples that
+ * straddle the face (twice the advecting velocity there), weighted by the
+ * direction's coefficient. Listing 1 prints this for su; sv is the same with
+ * x and y exchanged, and sw applies it on the w grid (horizontal advecting
+ * velocities are the sums of u or v at the two u-levels around w level k).
+ */
+typedef struct {
+    double q, a, b;  /* neighbour value; the two velocity samples at the face */
+} face;
+
+typedef struct {
+    face lo, hi;        /* lower (inflow) and upper (outflow) face */
+    double c_lo, c_hi;  /* their coefficients */
+    int horizontal;     /* one coefficient for both faces (tcx or tcy) */
+    int hi_on;          /* 0 where the scheme drops the upper face */
+} direction;
+
+static double flux(face f) { return f.q * (f.a + f.b); }
+
+/* The value of one direction: c (F_lo - F_hi) horizontally, as Listing 1
+ * groups it; c_lo F_lo - c_hi F_hi vertically. */
+static double dir_value(const direction *d)
+{
+    if (d->horizontal) return d->c_lo * (flux(d->lo) - flux(d->hi));
+    if (d->hi_on) return d->c_lo * flux(d->lo) - d->c_hi * flux(d->hi);
+    return d->c_lo * flux(d->lo);
+}
+
+/* Error scales of one direction. strict: |c| |q| |a + b| per face, the sum
+ * of the absolute values of the products the formula adds up. monomial:
+ * |c| |q| (|a| + |b|) per face, the same with each product expanded into
+ * its two monomials c q a and c q b. */
+static double dir_scale(const direction *d, int monomial)
+{
+    double lo = monomial ? absd(d->lo.a) + absd(d->lo.b) : absd(d->lo.a + d->lo.b);
+    double hi = monomial ? absd(d->hi.a) + absd(d->hi.b) : absd(d->hi.a + d->hi.b);
+    double s = absd(d->c_lo) * absd(d->lo.q) * lo;
+    if (d->hi_on) s += absd(d->c_hi) * absd(d->hi.q) * hi;
+    return s;
+}
+
+static face mkface(double q, double a, double b)
+{
+    face f;
+    f.q = q;
+    f.a = a;
+    f.b = b;
+    return f;
+}
+
+static direction mkdir(face lo, face hi, double c_lo, double c_hi, int horizontal, int hi_on)
+{
+    direction d;
+    d.lo = lo;
+    d.hi = hi;
+    d.c_lo = c_lo;
+    d.c_hi = c_hi;
+    d.horizontal = horizontal;
+    d.hi_on = hi_on;
+    return d;
+}
+
+/* The three directions of su, sv and sw at (k, j, i), k = 1 .. nz-1 (sw:
+ * k = 1 .. nz-2). dirs[0] is the output's own direction (x for su and sw, y
+ * for sv), so that sv is evaluated in the mirror order of su. */
+enum { OUT_SU = 0, OUT_SV = 1, OUT_SW = 2 };
+
+static void gather(int out, int k, int j, int i, int nz, long long sy, long long sz,
+                   const double *u, const double *v, const double *w,
+                   double tcx, double tcy, const double *tzc1, const double *tzc2,
+                   const double *tzd1, const double *tzd2, direction dirs[3])
+{
+    const int top = (k == nz - 1);
+    if (out == OUT_SU) {
+        /* x: u advected by u; y: u advected by v at the two faces j-1/2,
+         * j+1/2 of the u point; z: u advected by w at the faces below and
+         * above (dropped at the top level). */
+        dirs[0] = mkdir(mkface(AT(u, k, j, i - 1), AT(u, k, j, i - 1), AT(u, k, j, i)),
+                        mkface(AT(u, k, j, i + 1), AT(u, k, j, i), AT(u, k, j, i + 1)), tcx, tcx, 1, 1);
+        dirs[1] = mkdir(mkface(AT(u, k, j - 1, i), AT(v, k, j - 1, i), AT(v, k, j - 1, i + 1)),
+                        mkface(AT(u, k, j + 1, i), AT(v, k, j, i), AT(v, k, j, i + 1)), tcy, tcy, 1, 1);
+        dirs[2] = mkdir(mkface(AT(u, k - 1, j, i), AT(w, k - 1, j, i), AT(w, k - 1, j, i + 1)),
+                        mkface(top ? 0.0 : AT(u, k + 1, j, i), AT(w, k, j, i), AT(w, k, j, i + 1)),
+                        tzc1[k], tzc2[k], 0, !top);
+    } else if (out == OUT_SV) {
+        dirs[0] = mkdir(mkface(AT(v, k, j - 1, i), AT(v, k, j - 1, i), AT(v, k, j, i)),
+                        mkface(AT(v, k, j + 1, i), AT(v, k, j, i), AT(v, k, j + 1, i)), tcy, tcy, 1, 1);
+        dirs[1] = mkdir(mkface(AT(v, k, j, i - 1), AT(u, k, j, i - 1), AT(u, k, j + 1, i - 1)),
+                        mkface(AT(v, k, j, i + 1), AT(u, k, j, i), AT(u, k, j + 1, i)), tcx, tcx, 1, 1);
+        dirs[2] = mkdir(mkface(AT(v, k - 1, j, i), AT(w, k - 1, j, i), AT(w, k - 1, j + 1, i)),
+                        mkface(top ? 0.0 : AT(v, k + 1, j, i), AT(w, k, j, i), AT(w, k, j + 1, i)),
+                        tzc1[k], tzc2[k], 0, !top);
+    } else {
+        dirs[0] = mkdir(mkface(AT(w, k, j, i - 1), AT(u, k, j, i - 1), AT(u, k + 1, j, i - 1)),
+                        mkface(AT(w, k, j, i + 1), AT(u, k, j, i), AT(u, k + 1, j, i)), tcx, tcx, 1, 1);
+        dirs[1] = mkdir(mkface(AT(w, k, j - 1, i), AT(v, k, j - 1, i), AT(v, k + 1, j - 1, i)),
+                        mkface(AT(w, k, j + 1, i), AT(v, k, j, i), AT(v, k + 1, j, i)), tcy, tcy, 1, 1);
+        dirs[2] = mkdir(mkface(AT(w, k - 1, j, i), AT(w, k - 1, j, i), AT(w, k, j, i)),
+                        mkface(AT(w, k + 1, j, i), AT(w, k, j, i), AT(w, k + 1, j, i)),
+                        tzd1[k], tzd2[k], 0, 1);
+    }
+}
+
+/* Walk every interior point; per output: value (s != NULL) and error scale
+ * (a != NULL; monomial selects the scale). Level 1 and sw at level nz are 0. */
+static void walk(int nx, int ny, int nz, long long sy, long long sz,
+                 const double *u, const double *v, const double *w,
+                 double tcx, double tcy, const double *tzc1, const double *tzc2,
+                 const double *tzd1, const double *tzd2,
+                 double *const s[3], double *const a[3], int monomial, int nthreads)
 {
     if (nx < 1 || ny < 1 || nz < 1) return;
     if (nthreads < 1) nthreads = 1;
@@ -110,86 +223,114 @@ void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
 #endif
     for (int i = 1; i <= nx; ++i) {
         for (int j = 1; j <= ny; ++j) {
-            /* Level 1 (k = 0 here) is not computed. */
-            AT(su, 0, j, i) = 0.0;
-            AT(sv, 0, j, i) = 0.0;
-            AT(sw, 0, j, i) = 0.0;
-            if (asu) { AT(asu, 0, j, i) = 0.0; AT(asv, 0, j, i) = 0.0; AT(asw, 0, j, i) = 0.0; }
-
+            for (int o = 0; o < 3; ++o) {
+                if (s[o]) AT(s[o], 0, j, i) = 0.0;
+                if (a[o]) AT(a[o], 0, j, i) = 0.0;
+            }
             for (int k = 1; k < nz; ++k) {
-                const int top = (k == nz - 1);
-                double s, a;
-
-                /* su: Listing 1. x self term, y cross term with v, z cross term with w. */
-                s = tcx * (AT(u, k, j, i - 1) * (AT(u, k, j, i) + AT(u, k, j, i - 1))
-                           - AT(u, k, j, i + 1) * (AT(u, k, j, i) + AT(u, k, j, i + 1)));
-                s = s + tcy * (AT(u, k, j - 1, i) * (AT(v, k, j - 1, i) + AT(v, k, j - 1, i + 1))
-                               - AT(u, k, j + 1, i) * (AT(v, k, j, i) + AT(v, k, j, i + 1)));
-                if (!top) {
-                    s = s + tzc1[k] * AT(u, k - 1, j, i) * (AT(w, k - 1, j, i) + AT(w, k - 1, j, i + 1))
-                          - tzc2[k] * AT(u, k + 1, j, i) * (AT(w, k, j, i) + AT(w, k, j, i + 1));
-                } else {
-                    s = s + tzc1[k] * AT(u, k - 1, j, i) * (AT(w, k - 1, j, i) + AT(w, k - 1, j, i + 1));
-                }
-                AT(su, k, j, i) = s;
-                if (asu) {
-                    a = absd(tcx) * (absd(AT(u, k, j, i - 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k, j, i - 1)))
-                                     + absd(AT(u, k, j, i + 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k, j, i + 1))));
-                    a += absd(tcy) * (absd(AT(u, k, j - 1, i)) * (absd(AT(v, k, j - 1, i)) + absd(AT(v, k, j - 1, i + 1)))
-                                      + absd(AT(u, k, j + 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k, j, i + 1))));
-                    a += absd(tzc1[k]) * absd(AT(u, k - 1, j, i)) * (absd(AT(w, k - 1, j, i)) + absd(AT(w, k - 1, j, i + 1)));
-                    if (!top)
-                        a += absd(tzc2[k]) * absd(AT(u, k + 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k, j, i + 1)));
-                    AT(asu, k, j, i) = a;
-                }
-
-                /* sv: su with x and y exchanged (u <-> v, tcx <-> tcy). */
-                s = tcy * (AT(v, k, j - 1, i) * (AT(v, k, j, i) + AT(v, k, j - 1, i))
-                           - AT(v, k, j + 1, i) * (AT(v, k, j, i) + AT(v, k, j + 1, i)));
-                s = s + tcx * (AT(v, k, j, i - 1) * (AT(u, k, j, i - 1) + AT(u, k, j + 1, i - 1))
-                               - AT(v, k, j, i + 1) * (AT(u, k, j, i) + AT(u, k, j + 1, i)));
-                if (!top) {
-                    s = s + tzc1[k] * AT(v, k - 1, j, i) * (AT(w, k - 1, j, i) + AT(w, k - 1, j + 1, i))
-                          - tzc2[k] * AT(v, k + 1, j, i) * (AT(w, k, j, i) + AT(w, k, j + 1, i));
-                } else {
-                    s = s + tzc1[k] * AT(v, k - 1, j, i) * (AT(w, k - 1, j, i) + AT(w, k - 1, j + 1, i));
-                }
-                AT(sv, k, j, i) = s;
-                if (asv) {
-                    a = absd(tcy) * (absd(AT(v, k, j - 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k, j - 1, i)))
-                                     + absd(AT(v, k, j + 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k, j + 1, i))));
-                    a += absd(tcx) * (absd(AT(v, k, j, i - 1)) * (absd(AT(u, k, j, i - 1)) + absd(AT(u, k, j + 1, i - 1)))
-                                      + absd(AT(v, k, j, i + 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k, j + 1, i))));
-                    a += absd(tzc1[k]) * absd(AT(v, k - 1, j, i)) * (absd(AT(w, k - 1, j, i)) + absd(AT(w, k - 1, j + 1, i)));
-                    if (!top)
-                        a += absd(tzc2[k]) * absd(AT(v, k + 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k, j + 1, i)));
-                    AT(asv, k, j, i) = a;
-                }
-
-                /* sw: same flux form on the w grid. Horizontal advecting
-                 * velocities are the sums of u (v) at the two u-levels k and
-                 * k+1 around w-level k. Rigid lid: sw(nz) = 0. */
-                if (!top) {
-                    s = tcx * (AT(w, k, j, i - 1) * (AT(u, k, j, i - 1) + AT(u, k + 1, j, i - 1))
-                               - AT(w, k, j, i + 1) * (AT(u, k, j, i) + AT(u, k + 1, j, i)));
-                    s = s + tcy * (AT(w, k, j - 1, i) * (AT(v, k, j - 1, i) + AT(v, k + 1, j - 1, i))
-                                   - AT(w, k, j + 1, i) * (AT(v, k, j, i) + AT(v, k + 1, j, i)));
-                    s = s + tzd1[k] * AT(w, k - 1, j, i) * (AT(w, k, j, i) + AT(w, k - 1, j, i))
-                          - tzd2[k] * AT(w, k + 1, j, i) * (AT(w, k, j, i) + AT(w, k + 1, j, i));
-                    AT(sw, k, j, i) = s;
-                    if (asw) {
-                        a = absd(tcx) * (absd(AT(w, k, j, i - 1)) * (absd(AT(u, k, j, i - 1)) + absd(AT(u, k + 1, j, i - 1)))
-                                         + absd(AT(w, k, j, i + 1)) * (absd(AT(u, k, j, i)) + absd(AT(u, k + 1, j, i))));
-                        a += absd(tcy) * (absd(AT(w, k, j - 1, i)) * (absd(AT(v, k, j - 1, i)) + absd(AT(v, k + 1, j - 1, i)))
-                                          + absd(AT(w, k, j + 1, i)) * (absd(AT(v, k, j, i)) + absd(AT(v, k + 1, j, i))));
-                        a += absd(tzd1[k]) * absd(AT(w, k - 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k - 1, j, i)));
-                        a += absd(tzd2[k]) * absd(AT(w, k + 1, j, i)) * (absd(AT(w, k, j, i)) + absd(AT(w, k + 1, j, i)));
-                        AT(asw, k, j, i) = a;
+                for (int o = 0; o < 3; ++o) {
+                    if (!s[o] && !a[o]) continue;
+                    if (o == OUT_SW && k == nz - 1) { /* rigid lid */
+                        if (s[o]) AT(s[o], k, j, i) = 0.0;
+                        if (a[o]) AT(a[o], k, j, i) = 0.0;
+                        continue;
                     }
-                } else {
-                    AT(sw, k, j, i) = 0.0;
-                    if (asw) AT(asw, k, j, i) = 0.0;
+                    direction d[3];
+                    gather(o, k, j, i, nz, sy, sz, u, v, w, tcx, tcy, tzc1, tzc2, tzd1, tzd2, d);
+                    if (s[o]) {
+                        double t = dir_value(&d[0]);
+                        t = t + dir_value(&d[1]);
+                        t = t + dir_value(&d[2]);
+                        AT(s[o], k, j, i) = t;
+                    }
+                    if (a[o]) AT(a[o], k, j, i) = dir_scale(&d[0], monomial) + dir_scale(&d[1], monomial)
+                                                  + dir_scale(&d[2], monomial);
                 }
+            }
+        }
+    }
+}
+
+void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
+                const double *u, const double *v, const double *w,
+                double tcx, double tcy,
+                const double *tzc1, const double *tzc2,
+                const double *tzd1, const double *tzd2,
+                double *su, double *sv, double *sw,
+                double *asu, double *asv, double *asw, int nthreads)
+{
+    double *const s[3] = {su, sv, sw};
+    double *const a[3] = {asu, asv, asw};
+    walk(nx, ny, nz, sy, sz, u, v, w, tcx, tcy, tzc1, tzc2, tzd1, tzd2, s, a, 0, nthreads);
+}
+
+void pwo_monomial_scale(int nx, int ny, int nz, long long sy, long long sz,
+                        const double *u, const double *v, const double *w,
+                        double tcx, double tcy,
+                        const double *tzc1, const double *tzc2,
+                        const double *tzd1, const double *tzd2,
+                        double *msu, double *msv, double *msw, int nthreads)
+{
+    double *const s[3] = {NULL, NULL, NULL};
+    double *const a[3] = {msu, msv, msw};
+    walk(nx, ny, nz, sy, sz, u, v, w, tcx, tcy, tzc1, tzc2, tzd1, tzd2, s, a, 1, nthreads);
+}
+
+/*
+ * Energy weights. The flux form conserves the discrete kinetic energy of
+ * each wind component when the domain is periodic in x and y and w = 0 on
+ * the ground and at the lid: the fluxes through a face enter the budgets of
+ * the two cells that share it with opposite signs, once each cell's
+ * tendency is weighted by its mass, so the weighted sums telescope to 0.
+ * Mass of a u or v cell at level k: dz(k) rhon(k); of a w cell: dzn(k)
+ * rho(k), with dzn(k) = zn(k+1) - zn(k) as in pwo_coeffs (0 at levels 1
+ * and nz, where nothing is computed).
+ */
+int pwo_energy_weights(int nz, const double *dz, const double *rho, const double *rhon,
+                       double *wu, double *ww)
+{
+    if (nz < 1 || dz == NULL || wu == NULL || ww == NULL) return -1;
+    double *z = (double *)malloc(sizeof(double) * (size_t)nz);
+    double *zn = (double *)malloc(sizeof(double) * (size_t)nz);
+    if (!z || !zn) { free(z); free(zn); return -1; }
+    z[0] = 0.0;
+    for (int k = 1; k < nz; ++k) z[k] = z[k - 1] + dz[k];
+    for (int k = 1; k < nz; ++k) zn[k] = 0.5 * (z[k - 1] + z[k]);
+    zn[0] = (nz > 1) ? -zn[1] : 0.0;
+    for (int k = 0; k < nz; ++k) {
+        wu[k] = 0.0;
+        ww[k] = 0.0;
+    }
+    for (int k = 1; k < nz; ++k) wu[k] = dz[k] * (rhon ? rhon[k] : 1.0);
+    for (int k = 1; k < nz - 1; ++k) ww[k] = (zn[k + 1] - zn[k]) * (rho ? rho[k] : 1.0);
+    free(z);
+    free(zn);
+    return 0;
+}
+
+/*
+ * Energy budget: out[0..2] = sum over the interior of wu(k) u su, wu(k) v sv
+ * and ww(k) w sw; out[3..5] = the same sums of absolute values. Levels in
+ * order, rows in order, columns in order, one FP64 accumulator per sum.
+ */
+void pwo_energy_budget(int nx, int ny, int nz, long long sy, long long sz,
+                       const double *u, const double *v, const double *w,
+                       const double *su, const double *sv, const double *sw,
+                       const double *wu, const double *ww, double *out)
+{
+    for (int n = 0; n < 6; ++n) out[n] = 0.0;
+    for (int k = 0; k < nz; ++k) {
+        for (int j = 1; j <= ny; ++j) {
+            for (int i = 1; i <= nx; ++i) {
+                const double eu = wu[k] * AT(u, k, j, i) * AT(su, k, j, i);
+                const double ev = wu[k] * AT(v, k, j, i) * AT(sv, k, j, i);
+                const double ew = ww[k] * AT(w, k, j, i) * AT(sw, k, j, i);
+                out[0] += eu;
+                out[1] += ev;
+                out[2] += ew;
+                out[3] += absd(eu);
+                out[4] += absd(ev);
+                out[5] += absd(ew);
             }
         }
     }

@@ -34,9 +34,10 @@ int pwo_coeffs(int nz, double dx, double dy, const double *dz,
 /* Source terms su, sv, sw of Listing 1 (su) and its two companions (sv, sw).
  * Writes the interior i=1..nx, j=1..ny, every k; halo cells are untouched.
  * If asu/asv/asw are non-NULL they receive, per point, the sum of the
- * absolute values of the monomials c*x*y of the bilinear form at that point
- * (each flux c*x*(y+z) contributes |c||x|(|y|+|z|)): the scale against which
- * rounding error is measured. nthreads <= 0 means one thread. */
+ * absolute values of the products the formula adds up: each face term
+ * c*q*(a+b) contributes |c||q||a+b|. This is the scale against which the
+ * rounding error of an FP64 evaluation is measured.
+ * nthreads <= 0 means one thread. */
 void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
                 const double *u, const double *v, const double *w,
                 double tcx, double tcy,
@@ -44,6 +45,34 @@ void pwo_advect(int nx, int ny, int nz, long long sy, long long sz,
                 const double *tzd1, const double *tzd2,
                 double *su, double *sv, double *sw,
                 double *asu, double *asv, double *asw, int nthreads);
+
+/* The monomial error scale: per point, each face term c*q*(a+b) counted as
+ * its two monomials, |c||q|(|a|+|b|). It is >= the scale of pwo_advect and
+ * differs from it only where the two velocity samples of a face nearly
+ * cancel. It is the scale for evaluations that round the inputs a and b
+ * before adding them (each rounding is relative to |a| or |b|, not to
+ * |a+b|). Interior only; halo cells are untouched. */
+void pwo_monomial_scale(int nx, int ny, int nz, long long sy, long long sz,
+                        const double *u, const double *v, const double *w,
+                        double tcx, double tcy,
+                        const double *tzc1, const double *tzc2,
+                        const double *tzd1, const double *tzd2,
+                        double *msu, double *msv, double *msw, int nthreads);
+
+/* Mass weights of the discrete energy budget: wu[k] = dz(k) rhon(k) for the
+ * u and v cells, ww[k] = dzn(k) rho(k) for the w cells (dzn as in
+ * pwo_coeffs), 0 at the levels nothing is computed on (wu at level 1, ww at
+ * levels 1 and nz). rho/rhon may be NULL (1). Returns 0 or -1. */
+int pwo_energy_weights(int nz, const double *dz, const double *rho, const double *rhon,
+                       double *wu, double *ww);
+
+/* out[0..2] = sum over the interior of wu(k)*u*su, wu(k)*v*sv, ww(k)*w*sw;
+ * out[3..5] = the sums of the absolute values of the same summands. Fixed
+ * order (levels, rows, columns), one FP64 accumulator each. */
+void pwo_energy_budget(int nx, int ny, int nz, long long sy, long long sz,
+                       const double *u, const double *v, const double *w,
+                       const double *su, const double *sv, const double *sw,
+                       const double *wu, const double *ww, double *out);
 
 /* Transpose of the Jacobian of (u,v,w) -> (su,sv,sw) at (u,v,w), applied to
  * cotangents (gsu,gsv,gsw) given on the interior; result ADDED into

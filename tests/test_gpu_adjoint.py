@@ -1,8 +1,8 @@
 """GPU checks of the adjoint (pw_advect_adjoint), the halo fold and the
 autograd/rollout layer: against the oracle's scatter-form adjoint, the
 dot-product test <J d, y> = <d, J^T y> (1e-12 in FP64), finite differences
-of a checkpointed 20-step forward-Euler rollout, and exact transposition of
-the periodic halo fill.
+of one evaluation and of a checkpointed 20-step forward-Euler rollout (1e-8
+relative), and exact transposition of the periodic halo fill.
 """
 import numpy as np
 import pytest
@@ -152,11 +152,53 @@ def test_autograd_backward_is_adjoint(gpu):
         assert torch.allclose(g, wnt, rtol=0, atol=1e-13 * float(wnt.abs().max()))
 
 
+def _fd_noise_free_dot(torch, outs_p, outs_m, y, inner, h):
+    """sum y * (F(x + h d) - F(x - h d)) / (2h), differenced element by
+    element before the sum so that the sum's own rounding stays at the size
+    of the differences, not of F."""
+    return sum(float(((op[inner] - om[inner]) * yy[inner]).sum()) for op, om, yy in zip(outs_p, outs_m, y)) / (2 * h)
+
+
+@pytest.mark.parametrize("mode", ["f64", "paired"])
+def test_adjoint_finite_difference_single_step(gpu, mode):
+    """One evaluation of the 256 x 256 x 64 workload: the map is quadratic,
+    so a central difference with step 1e-6 equals the directional
+    derivative up to rounding, and <y, (F(x+hd) - F(x-hd)) / 2h> must
+    match <J^T y, d> from the adjoint kernel to 1e-8 relative. The
+    difference is taken of the native FP64 forward map for both adjoint
+    arithmetics."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 256, 256, 64
+    c = pw.make_coeffs(nz, 50.0, 50.0, synth.dz_stretched(nz)).to_device()
+    x = [to_device(a, nx, torch.float64) for a in synth.fields_iid(nx, ny, nz, seed=1)]
+    y = [to_device(_raw(nx, ny, nz, 91, s), nx, torch.float64) for s in range(3)]
+    d = [to_device(_raw(nx, ny, nz, 92, s, -10.0, 10.0), nx, torch.float64) for s in range(3)]
+    inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
+    for t in y:
+        keep = torch.zeros_like(t)
+        keep[inner] = t[inner]
+        t.copy_(keep)
+    h = 1e-6
+    fp = pw.advect(*[a + h * b for a, b in zip(x, d)], c, nx, ny, mode="f64")
+    fm = pw.advect(*[a - h * b for a, b in zip(x, d)], c, nx, ny, mode="f64")
+    g = pw.advect_adjoint(*x, c, nx, ny, *y, mode=mode)
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    fd = _fd_noise_free_dot(torch, fp, fm, y, inner, h)
+    an = sum(float((gg[:, :, : nx + 2] * dd[:, :, : nx + 2]).sum()) for gg, dd in zip(g, d))
+    print(f"{mode}: fd {fd!r} adjoint {an!r} rel {abs(fd - an) / abs(an):.3e}")
+    assert abs(fd - an) <= 1e-8 * abs(an), (fd, an)
+
+
 def test_rollout_gradient_checkpointed_and_fd(gpu):
     """20-step forward-Euler rollout (dt = 0.5 s) of the 256 x 256 x 64
     workload's winds, differentiated with checkpoints every 5 steps: the
     gradient equals the uncheckpointed one exactly, and a central finite
-    difference with step 1e-6 along a random direction matches it."""
+    difference with step 1e-6 along a random direction of the winds' size
+    matches it to 1e-8 relative. (The rollout is a polynomial of high
+    degree, so the difference carries an O(h^2) term besides rounding; at
+    this step both stay below 1e-8.)"""
     from paper_2107_13500_gb300 import autograd as pa
     from paper_2107_13500_gb300 import pw
     torch = gpu
@@ -168,9 +210,11 @@ def test_rollout_gradient_checkpointed_and_fd(gpu):
     y = [to_device(_raw(nx, ny, nz, 81, s), nx, torch.float64) for s in range(3)]
     inner = (slice(None), slice(1, ny + 1), slice(1, nx + 1))
 
+    def rollout(xs, ckpt):
+        return pa.rollout(*xs, c, nx, ny, 0.5, 20, mode="f64", checkpoint_every=ckpt)
+
     def objective(xs, ckpt):
-        out = pa.rollout(*xs, c, nx, ny, 0.5, 20, mode="f64", checkpoint_every=ckpt)
-        return sum((o[inner] * yy[inner]).sum() for o, yy in zip(out, y))
+        return sum((o[inner] * yy[inner]).sum() for o, yy in zip(rollout(xs, ckpt), y))
 
     xs = [t.clone().requires_grad_() for t in x0]
     g_ck = torch.autograd.grad(objective(xs, 5), xs)
@@ -178,7 +222,7 @@ def test_rollout_gradient_checkpointed_and_fd(gpu):
     g_full = torch.autograd.grad(objective(xs2, 0), xs2)
     for a, b in zip(g_ck, g_full):
         assert torch.equal(a, b)
-    d = [to_device(_raw(nx, ny, nz, 82, s), nx, torch.float64) for s in range(3)]
+    d = [to_device(_raw(nx, ny, nz, 82, s, -10.0, 10.0), nx, torch.float64) for s in range(3)]
     for t in d:
         t[:, 0, :] = 0
         t[:, ny + 1, :] = 0
@@ -186,11 +230,12 @@ def test_rollout_gradient_checkpointed_and_fd(gpu):
         t[:, :, nx + 1] = 0
     h = 1e-6
     with torch.no_grad():
-        jp = float(objective([a + h * b for a, b in zip(x0, d)], 0))
-        jm = float(objective([a - h * b for a, b in zip(x0, d)], 0))
-    fd = (jp - jm) / (2 * h)
+        op = rollout([a + h * b for a, b in zip(x0, d)], 0)
+        om = rollout([a - h * b for a, b in zip(x0, d)], 0)
+    fd = _fd_noise_free_dot(torch, op, om, y, inner, h)
     an = sum(float((g * dd).sum()) for g, dd in zip(g_ck, d))
-    assert abs(fd - an) <= 1e-6 * max(abs(an), 1.0), (fd, an)
+    print(f"rollout: fd {fd!r} adjoint {an!r} rel {abs(fd - an) / abs(an):.3e}")
+    assert abs(fd - an) <= 1e-8 * abs(an), (fd, an)
 
 
 @pytest.mark.parametrize("mode", ["f64", "paired", "f32"])

@@ -8,7 +8,7 @@ the edge cases of the method (nz = 1, 2, 3; one-column domains), the full
 import numpy as np
 import pytest
 
-from helpers import TOL_F64, compare_f64, interior, to_device, to_numpy_f64
+from helpers import check_mode, compare_f32, compare_paired, interior, to_device, to_numpy_f64
 from paper_2107_13500_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -31,13 +31,14 @@ def _run(gpu, mode, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, oracle
     torch = gpu
     co = oracle_lib.coeffs(nz, dx, dy, dz, rho, rhon)
     (so, ab) = oracle_lib.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=8)
+    mb = oracle_lib.monomial_scale(u, v, w, co, nx, ny, nthreads=8) if mode == "paired" else None
     c = pw.make_coeffs(nz, dx, dy, dz, rho, rhon).to_device()
     du, dv, dw = (to_device(f, nx, torch.float64, aligned=aligned) for f in (u, v, w))
     out = pw.advect(du, dv, dw, c, nx, ny, mode=mode)
     torch.cuda.synchronize()
     assert pw.device_status() == 0
     g = [to_numpy_f64(t, u.shape[2], nx) for t in out]
-    return g, so, ab
+    return g, so, (ab, mb)
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
@@ -47,7 +48,7 @@ def test_small_iid_config(gpu, oracle_lib, mode):
     u, v, w = cfg["fields"]()
     g, o, a = _run(gpu, mode, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"],
                    oracle_lib=oracle_lib)
-    compare_f64(g, o, a, cfg["nx"], cfg["ny"])
+    check_mode(mode, g, o, *a, cfg["nx"], cfg["ny"])
 
 
 @pytest.mark.parametrize("aligned", [True, False])
@@ -61,7 +62,7 @@ def test_ragged_stretched_density(gpu, oracle_lib, mode, shape, aligned):
     rho, rhon = synth.density_exponential(dz)
     u, v, w = synth.fields_iid(nx, ny, nz, seed=nx * 7 + ny)
     g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 40.0, 60.0, dz, rho, rhon, oracle_lib, aligned)
-    compare_f64(g, o, a, nx, ny)
+    check_mode(mode, g, o, *a, nx, ny)
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
@@ -73,7 +74,7 @@ def test_degenerate_shapes(gpu, oracle_lib, mode, shape):
     dz = synth.dz_uniform(nz, 20.0)
     u, v, w = synth.fields_iid(nx, ny, nz, seed=99)
     g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 50.0, 50.0, dz, oracle_lib=oracle_lib)
-    compare_f64(g, o, a, nx, ny)
+    check_mode(mode, g, o, *a, nx, ny)
     if nz == 1:
         for s in g:
             assert np.all(interior(s, nx, ny) == 0.0)
@@ -90,7 +91,7 @@ def test_tall_columns_many_level_chunks(gpu, oracle_lib, mode, shape):
     rho, rhon = synth.density_exponential(dz)
     u, v, w = synth.fields_iid(nx, ny, nz, seed=nz)
     g, o, a = _run(gpu, mode, u, v, w, nx, ny, nz, 50.0, 50.0, dz, rho, rhon, oracle_lib=oracle_lib)
-    compare_f64(g, o, a, nx, ny)
+    check_mode(mode, g, o, *a, nx, ny)
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
@@ -112,8 +113,8 @@ def test_full_16m_modes_config(gpu, oracle_lib, mode):
     u, v, w = cfg["fields"]()
     g, o, a = _run(gpu, mode, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"],
                    oracle_lib=oracle_lib)
-    worst = compare_f64(g, o, a, cfg["nx"], cfg["ny"])
-    print("worst (err/A, normwise):", worst)
+    worst = check_mode(mode, g, o, *a, cfg["nx"], cfg["ny"])
+    print("worst:", worst)
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
@@ -125,7 +126,62 @@ def test_full_134m_iid_config(gpu, oracle_lib, mode):
     g, o, a = _run(gpu, mode, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"],
                    oracle_lib=oracle_lib)
     del u, v, w
-    print("worst (err/A, normwise):", compare_f64(g, o, a, cfg["nx"], cfg["ny"]))
+    print("worst:", check_mode(mode, g, o, *a, cfg["nx"], cfg["ny"]))
+
+
+@pytest.mark.parametrize("e", [40, -40])
+def test_paired_inputs_scaled_by_powers_of_two(gpu, oracle_lib, e):
+    """The paired path carries FP32's exponent range. Winds scaled by 2^40
+    and 2^-40 (magnitudes up to 2^43.4 and down to the smallest i.i.d.
+    values near 2^-50) on a stretched grid with density, ragged tiles:
+    every point stays within the paired tolerance of the oracle evaluated
+    on the same scaled winds."""
+    nx, ny, nz = 53, 19, 14
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    u, v, w = (f * 2.0 ** e for f in synth.fields_iid(nx, ny, nz, seed=40 + e))
+    g, o, a = _run(gpu, "paired", u, v, w, nx, ny, nz, 50.0, 50.0, dz, rho, rhon, oracle_lib)
+    print("worst (err/M, err/A, normwise):", compare_paired(g, o, *a, nx, ny))
+
+
+def _run_f32(gpu, oracle_lib, u, v, w, nx, ny, nz, dx, dy, dz, rho=None, rhon=None, aligned=True):
+    """PW_F32 on float copies of u, v, w; the oracle on the double fields."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    co = oracle_lib.coeffs(nz, dx, dy, dz, rho, rhon)
+    so = oracle_lib.advect(u, v, w, co, nx, ny, nthreads=8)
+    mb = oracle_lib.monomial_scale(u, v, w, co, nx, ny, nthreads=8)
+    c = pw.make_coeffs(nz, dx, dy, dz, rho, rhon).to_device()
+    du, dv, dw = (to_device(f, nx, torch.float32, aligned=aligned) for f in (u, v, w))
+    out = pw.advect(du, dv, dw, c, nx, ny, mode="f32")
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    g = [to_numpy_f64(t.double(), u.shape[2], nx) for t in out]
+    return compare_f32(g, so, mb, nx, ny)
+
+
+@pytest.mark.parametrize("aligned", [True, False])
+@pytest.mark.parametrize("shape", [(37, 13, 5), (100, 17, 11), (131, 9, 7), (5, 4, 2)])
+def test_f32_full_fields_ragged(gpu, oracle_lib, shape, aligned):
+    """Plain FP32 (float winds, float arithmetic) against the FP64 oracle on
+    the original double winds: ragged tiles, stretched grid with density,
+    both interior alignments."""
+    nx, ny, nz = shape
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz)
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=nx + 3 * ny)
+    print("worst (err/M, max rel, rms rel):",
+          _run_f32(gpu, oracle_lib, u, v, w, nx, ny, nz, 40.0, 60.0, dz, rho, rhon, aligned))
+
+
+@pytest.mark.parametrize("cfg_name", ["config_small_iid", "config_16m_modes"])
+def test_f32_full_fields_configs(gpu, oracle_lib, cfg_name):
+    """Plain FP32 on the 64^3 i.i.d. and the 512 x 512 x 64 smooth-wind
+    workloads, point by point against the oracle."""
+    cfg = getattr(synth, cfg_name)()
+    u, v, w = cfg["fields"]()
+    print("worst (err/M, max rel, rms rel):",
+          _run_f32(gpu, oracle_lib, u, v, w, cfg["nx"], cfg["ny"], cfg["nz"], cfg["dx"], cfg["dy"], cfg["dz"]))
 
 
 @pytest.mark.parametrize("aligned", [True, False])
@@ -244,7 +300,7 @@ def test_bounded_wait_gives_up_and_device_stays_usable(gpu, oracle_lib):
     u, v, w = synth.fields_iid(nx, ny, nz, seed=5)
     g, o, a = _run(gpu, "paired", u, v, w, nx, ny, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0),
                    oracle_lib=oracle_lib)
-    compare_f64(g, o, a, nx, ny)
+    check_mode("paired", g, o, *a, nx, ny)
 
 
 @pytest.mark.parametrize("mode", ["paired", "f32", "f64"])
