@@ -237,7 +237,7 @@ size_t pw_batch_plan_bytes(int n);
  * 1 = 64x4; 2 = 32x8; 3 = 64x8; 4 = 32x16; 5 = 128x2 (all 4 levels);
  * 6 = 64x4, 3 levels; 7 = 64x4, 6 levels.
  * PW_F64_PAIRED: 0 = 32x8, 2 levels; 1 = 32x4; 2 = 32x16 (2 levels);
- * 3 = 32x8, 3 levels. PW_F64: 0 (not batched). */
+ * 3 = 32x8, 3 levels. PW_F64: 0 = 32x16, 1 = 32x8 (4-level rings). */
 int pw_variant_count(pw_dtype dtype);
 
 /*
@@ -247,9 +247,9 @@ int pw_variant_count(pw_dtype dtype);
  * pw_batch_plan_bytes(n)). Domains are ordered tallest first. *n_items
  * receives the number of work items. The caller copies the plan to a device
  * buffer (64-byte aligned) and passes it to pw_advect_batched; the device
- * buffer is also the kernel's work-queue scratch. dtype PW_F64_PAIRED,
- * PW_F32 or PW_F32_SPLIT. Errors: PW_ENULL, PW_EINVAL, PW_EALIAS,
- * PW_EUNSUPPORTED, PW_ECUDA (descriptor encoding).
+ * buffer is also the kernel's work-queue scratch. Any dtype. Errors:
+ * PW_ENULL, PW_EINVAL, PW_EALIAS, PW_EUNSUPPORTED, PW_ECUDA (descriptor
+ * encoding).
  */
 int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain *doms, int variant, void *plan_host,
                        size_t plan_bytes, long long *n_items);
@@ -260,7 +260,8 @@ int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain *doms, int variant
  * resident CTAs per SM, at most n_items). dtype and variant must be those the
  * plan was built with (a mismatch is reported by pw_device_status as
  * PW_EINVAL, outputs unspecified). Launches on the same plan must not overlap
- * on the GPU (they share its counter). Capturable in a CUDA graph.
+ * on the GPU (they share its counter). Capturable in a CUDA graph (the
+ * counter reset is a memset node). Any dtype.
  * Errors: PW_ENULL, PW_EINVAL, PW_EUNSUPPORTED, PW_ECUDA.
  */
 int pw_advect_batched(pw_dtype dtype, int variant, void *plan_dev, long long n_items, void *stream);
@@ -269,23 +270,26 @@ int pw_advect_batched(pw_dtype dtype, int variant, void *plan_dev, long long n_i
  * pw_advect_batched_noalloc -- pw_advect_batched for callers that cannot
  * allocate device memory. (The paper has no counterpart: this is a property
  * of the library, not of the method.) pw_advect_batched needs the batch plan
- * in a device buffer the caller allocates; code that is capturing a CUDA
- * graph, real-time loops that must not call cudaMalloc (it can synchronise
- * the device), and programs whose device memory is wholly reserved by
- * another allocator cannot make that buffer. This entry point takes the HOST
- * plan from pw_make_batch_plan instead and copies it, on `stream`, into a
- * fixed device array inside the library (room for PW_NOALLOC_MAX_DOMAINS
+ * in a device buffer the caller allocates. Some callers cannot make one:
+ * real-time loops that must not call cudaMalloc (it can synchronise the
+ * device and its latency is unbounded), plug-ins that run inside a host
+ * program which owns every device allocation, and programs whose device
+ * memory is wholly reserved by another allocator. This entry point takes the
+ * HOST plan from pw_make_batch_plan instead and copies it, on `stream`, into
+ * a fixed device array inside the library (room for PW_NOALLOC_MAX_DOMAINS
  * domains, about 150 KB, which every GPU that loads the library holds until
  * the process exits), zeroes the work counter there and launches the same
  * persistent kernel. It calls no cudaMalloc, cudaFree or allocating library
  * routine. The first call on a device looks up the array's address on that
- * device (make that call, with the device current, before any stream
- * capture). Every call on a device shares the one array: calls whose work
+ * device, with the device current; make that first call before any stream
+ * capture. plan_host may be pageable (the copy is staged before the call
+ * returns) or pinned (then it must stay unchanged until the copy has run on
+ * `stream`). Every call on a device shares the one array: calls whose work
  * overlaps on the GPU race and produce unspecified results, so order them
  * (same stream, or events). Plans with more than PW_NOALLOC_MAX_DOMAINS
- * domains are rejected with PW_EINVAL. Its own errors are reported through
- * pw_noalloc_last_error. Errors: PW_ENULL, PW_EINVAL, PW_EUNSUPPORTED,
- * PW_ECUDA.
+ * domains are rejected with PW_EINVAL. dtype PW_F64_PAIRED, PW_F32 or
+ * PW_F32_SPLIT. Its own errors are reported through pw_noalloc_last_error.
+ * Errors: PW_ENULL, PW_EINVAL, PW_EUNSUPPORTED, PW_ECUDA.
  */
 #define PW_NOALLOC_MAX_DOMAINS 256
 int pw_advect_batched_noalloc(pw_dtype dtype, int variant, const void *plan_host, size_t plan_bytes,
@@ -293,6 +297,40 @@ int pw_advect_batched_noalloc(pw_dtype dtype, int variant, const void *plan_host
 
 /* Message for the last failure of pw_advect_batched_noalloc in this thread. */
 const char *pw_noalloc_last_error(void);
+
+/*
+ * pw_make_energy_weights -- host masses of the energy budget (no GPU work).
+ * wu_host[k] = dz(k) rhon(k), the mass of the u and v cells of level k;
+ * ww_host[k] = dzn(k) rho(k), the mass of the w cell around w level k, with
+ * dzn as in pw_make_coeffs; 0 at the levels nothing is computed on (wu at
+ * level 1, ww at levels 1 and nz). dz, rho, rhon as for pw_make_coeffs.
+ * Errors: PW_ENULL, PW_EINVAL.
+ */
+int pw_make_energy_weights(int nz, const double *dz, const double *rho, const double *rhon, double *wu_host,
+                           double *ww_host);
+
+/*
+ * pw_energy_budget -- FP64 conservation diagnostic of a set of source
+ * terms. The paper accelerates the Piacsek-Williams scheme (Sec. I) in the
+ * flux form of Listing 1: on a domain periodic in x and y with w = 0 on the
+ * ground and at the lid, the flux through each face enters the two cells
+ * that share it with opposite signs, so the mass-weighted energy tendencies
+ *   sum wu(k) u su,  sum wu(k) v sv,  sum ww(k) w sw   (over the interior)
+ * vanish in exact arithmetic. This call measures how far a path's rounding
+ * moves them from 0. level_sums (DEVICE, 6*nz doubles) receives per level k
+ * the interior sums [u su, v sv, w sw, |u su|, |v sv|, |w sw|] (unweighted);
+ * totals (DEVICE, 6 doubles) the same weighted by wu (u, v) and ww (w) and
+ * added over the levels in order. All arithmetic is FP64 in a fixed order,
+ * so the result is repeatable. Winds (u, v, w; layout dims_wind) and
+ * tendencies (su, sv, sw; layout dims_tend, same nx, ny, nz) are each float
+ * or double (elem_bytes 4 or 8), e.g. the FP64 winds and the float source
+ * terms of the PW_F32_SPLIT path. wu, ww: DEVICE arrays of nz doubles (from
+ * pw_make_energy_weights). Asynchronous on `stream`; nz <= 65535.
+ * Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_ECUDA.
+ */
+int pw_energy_budget(const void *u, const void *v, const void *w, int wind_elem_bytes, const pw_dims *dims_wind,
+                     const void *su, const void *sv, const void *sw, int tend_elem_bytes, const pw_dims *dims_tend,
+                     const double *wu, const double *ww, double *level_sums, double *totals, void *stream);
 
 /*
  * pw_device_status -- read and clear the library's device error word on the

@@ -347,6 +347,63 @@ extern "C" int pw_split_field(const double* f, const pw_dims* dims_f, float* fp,
     return PW_OK;
 }
 
+extern "C" int pw_make_energy_weights(int nz, const double* dz, const double* rho, const double* rhon,
+                                      double* wu_host, double* ww_host) {
+    const char* who = "pw_make_energy_weights";
+    if (!dz || !wu_host || !ww_host) return fail(PW_ENULL, "%s: dz, wu_host and ww_host are required", who);
+    if (nz < 1) return fail(PW_EINVAL, "%s: nz must be >= 1", who);
+    for (int k = 1; k < nz; ++k)
+        if (!(dz[k] > 0.0)) return fail(PW_EINVAL, "%s: dz[%d] must be > 0", who, k);
+    // u-level heights (as pw_make_coeffs): zu(k) midway between w levels k-1, k
+    std::vector<double> zw(nz), zu(nz);
+    double top = 0.0;
+    zw[0] = 0.0;
+    for (int k = 1; k < nz; ++k) {
+        top += dz[k];
+        zw[k] = top;
+        zu[k] = 0.5 * (zw[k - 1] + zw[k]);
+    }
+    zu[0] = nz > 1 ? -zu[1] : 0.0;
+    for (int k = 0; k < nz; ++k) wu_host[k] = ww_host[k] = 0.0;
+    for (int k = 1; k < nz; ++k) wu_host[k] = dz[k] * (rhon ? rhon[k] : 1.0);
+    for (int k = 1; k + 1 < nz; ++k) ww_host[k] = (zu[k + 1] - zu[k]) * (rho ? rho[k] : 1.0);
+    return PW_OK;
+}
+
+extern "C" int pw_energy_budget(const void* u, const void* v, const void* w, int wind_elem_bytes,
+                                const pw_dims* dims_wind, const void* su, const void* sv, const void* sw,
+                                int tend_elem_bytes, const pw_dims* dims_tend, const double* wu, const double* ww,
+                                double* level_sums, double* totals, void* stream) {
+    const char* who = "pw_energy_budget";
+    if ((wind_elem_bytes != 4 && wind_elem_bytes != 8) || (tend_elem_bytes != 4 && tend_elem_bytes != 8))
+        return fail(PW_EINVAL, "%s: element sizes must be 4 or 8 bytes", who);
+    int rc = check_dims(dims_wind, wind_elem_bytes, who);
+    if (rc) return rc;
+    if ((rc = check_dims(dims_tend, tend_elem_bytes, who))) return rc;
+    if (dims_wind->nx != dims_tend->nx || dims_wind->ny != dims_tend->ny || dims_wind->nz != dims_tend->nz)
+        return fail(PW_EINVAL, "%s: the winds and the tendencies describe different domains", who);
+    if (dims_wind->nz > 65535) return fail(PW_EINVAL, "%s: nz above 65535", who);
+    const void* wp[3] = {u, v, w};
+    const void* sp[3] = {su, sv, sw};
+    const char* wn[3] = {"u", "v", "w"};
+    const char* sn[3] = {"su", "sv", "sw"};
+    for (int n = 0; n < 3; ++n) {
+        if ((rc = check_ptr(wp[n], wind_elem_bytes, wn[n], who))) return rc;
+        if ((rc = check_ptr(sp[n], tend_elem_bytes, sn[n], who))) return rc;
+    }
+    if (!wu || !ww || !level_sums || !totals) return fail(PW_ENULL, "%s: wu, ww, level_sums and totals are required", who);
+    if (((uintptr_t)wu | (uintptr_t)ww | (uintptr_t)level_sums | (uintptr_t)totals) % 8)
+        return fail(PW_EINVAL, "%s: misaligned weight or result array", who);
+    const long long nz = dims_wind->nz;
+    if (overlap(level_sums, 48 * nz, totals, 48)) return fail(PW_EALIAS, "%s: level_sums overlaps totals", who);
+    cudaError_t e = pw::launch_energy_budget(u, v, w, wind_elem_bytes, dims_wind->sy, dims_wind->sz, su, sv, sw,
+                                             tend_elem_bytes, dims_tend->sy, dims_tend->sz, dims_wind->nx,
+                                             dims_wind->ny, dims_wind->nz, wu, ww, level_sums, totals,
+                                             static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, who);
+    return PW_OK;
+}
+
 extern "C" int pw_selftest_bounded_wait(unsigned int limit_us, int* status, void* stream) {
     const char* who = "pw_selftest_bounded_wait";
     if (!status) return fail(PW_ENULL, "%s: status is NULL", who);
@@ -444,6 +501,7 @@ extern "C" int pw_variant_count(pw_dtype dtype) {
         case PW_F32:
         case PW_F32_SPLIT: return pw::split_variant_count();
         case PW_F64_PAIRED: return pw::paired_variant_count();
+        case PW_F64: return pw::f64_variant_count();
         default: return 0;
     }
 }
@@ -453,7 +511,6 @@ extern "C" int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain* doms, 
     const char* who = "pw_make_batch_plan";
     if (!doms || !plan_host || !n_items) return fail(PW_ENULL, "%s: doms, plan_host and n_items are required", who);
     if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
-    if (dtype == PW_F64) return fail(PW_EUNSUPPORTED, "%s: PW_F64 has no batched kernel (use PW_F64_PAIRED)", who);
     if (n < 1) return fail(PW_EINVAL, "%s: n must be >= 1", who);
     if (variant < 0 || variant >= pw_variant_count(dtype))
         return fail(PW_EINVAL, "%s: variant %d out of range for this dtype", who, variant);
@@ -461,7 +518,9 @@ extern "C" int pw_make_batch_plan(pw_dtype dtype, int n, const pw_domain* doms, 
         return fail(PW_EINVAL, "%s: plan_bytes %zu < %zu", who, plan_bytes, pw::batch_plan_bytes(n));
     if (((uintptr_t)plan_host) % 64 != 0) return fail(PW_EINVAL, "%s: plan_host must be 64-byte aligned", who);
     const int es = elem_size(dtype);
-    const pw::TileShape shp = dtype == PW_F64_PAIRED ? pw::fwd_paired_shape_variant(variant) : pw::fwd_split_shape_variant(variant);
+    const pw::TileShape shp = dtype == PW_F64_PAIRED ? pw::fwd_paired_shape_variant(variant)
+                              : dtype == PW_F64    ? pw::fwd_f64_shape_variant(variant)
+                                                   : pw::fwd_split_shape_variant(variant);
     // tallest domains first: their tiles take longest, so they start first
     std::vector<int> order(n);
     for (int d = 0; d < n; ++d) order[d] = d;
@@ -540,9 +599,7 @@ extern "C" int pw_advect_batched(pw_dtype dtype, int variant, void* plan_dev, lo
     const char* who = "pw_advect_batched";
     if (!plan_dev) return fail(PW_ENULL, "%s: plan_dev is NULL", who);
     if (((uintptr_t)plan_dev) % 64 != 0) return fail(PW_EINVAL, "%s: plan_dev must be 64-byte aligned", who);
-    if (dtype != PW_F64_PAIRED && dtype != PW_F32 && dtype != PW_F32_SPLIT)
-        return fail(known_dtype(dtype) ? PW_EUNSUPPORTED : PW_EINVAL, "%s: no batched kernel for dtype %d", who,
-                    (int)dtype);
+    if (!known_dtype(dtype)) return fail(PW_EINVAL, "%s: unknown dtype %d", who, (int)dtype);
     if (variant < 0 || variant >= pw_variant_count(dtype)) return fail(PW_EINVAL, "%s: bad variant", who);
     if (n_items < 1) return fail(PW_EINVAL, "%s: n_items must be >= 1", who);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -550,6 +607,7 @@ extern "C" int pw_advect_batched(pw_dtype dtype, int variant, void* plan_dev, lo
     cudaError_t e = cudaMemsetAsync(&plan->counter, 0, sizeof(plan->counter), st);
     if (e != cudaSuccess) return cuda_fail(e, who);
     e = dtype == PW_F64_PAIRED ? pw::launch_paired_batched(variant, plan, n_items, st)
+        : dtype == PW_F64      ? pw::launch_f64_batched(variant, plan, n_items, st)
                                : pw::launch_split_batched(variant, plan, n_items, st);
     if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;

@@ -1,5 +1,5 @@
 // pw_internal.h -- launchers shared between the C ABI (pw_api.cu) and the
-// kernel translation unit (pw_kernels.cu). Not part of the public ABI.
+// kernel translation units. Not part of the public ABI.
 #pragma once
 
 #include <cuda.h>
@@ -253,6 +253,9 @@ cudaError_t choose_sched(Kern kern, int threads, int smem, int tiles_x, int tile
     return cudaSuccess;
 }
 
+int f64_variant_count();
+TileShape fwd_f64_shape_variant(int v);
+cudaError_t launch_f64_batched(int v, BatchPlan* plan, long long n_items, cudaStream_t st);
 int split_variant_count();
 TileShape fwd_split_shape_variant(int v);
 cudaError_t launch_fwd_split_variant(int v, const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
@@ -295,10 +298,16 @@ cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, fl
 
 cudaError_t launch_selftest_wait(unsigned long long limit_ns, cudaStream_t st);
 
+cudaError_t launch_energy_budget(const void* u, const void* v, const void* w, int wind_bytes, long long wsy,
+                                 long long wsz, const void* su, const void* sv, const void* sw, int tend_bytes,
+                                 long long ssy, long long ssz, int nx, int ny, int nz, const double* wu,
+                                 const double* ww, double* level_sums, double* totals, cudaStream_t st);
+
 // Read and clear the device status words of every kernel unit (synchronises st).
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_paired(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_split(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_adjoint(unsigned int* status, cudaStream_t st);
+cudaError_t read_and_clear_status_f64(unsigned int* status, cudaStream_t st);
 
 }  // namespace pw

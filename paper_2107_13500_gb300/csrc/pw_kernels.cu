@@ -1,11 +1,8 @@
-// pw_kernels.cu -- PW advection kernels for sm_103a and their launchers.
-//
-// Forward kernels (one CTA per TX x TY tile of columns, k-march with a TMA
-// ring, see pw_ring.cuh):
-//   fwd_f64     native FP64 arithmetic (the straightforward baseline);
-//   fwd_paired  FP64 in/out, paired-FP32 arithmetic (pw_paired.cuh);
-//   fwd_split   FP32 perturbations about per-level FP64 means.
-// Helpers: periodic halo fill and the per-level mean/perturbation split.
+// pw_kernels.cu -- helper kernels of the PW advection library: periodic halo
+// fill, the per-level mean/perturbation split, the bounded-wait self-test
+// and the device status word. The forward kernels live in pw_f64.cu (native
+// FP64), pw_paired.cu (paired FP32) and pw_split.cu (FP32); the adjoint in
+// pw_adjoint.cu.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
@@ -18,162 +15,6 @@
 namespace pw {
 
 namespace cg = cooperative_groups;
-
-// ---------------------------------------------------------------------------
-// Native FP64 forward kernel.
-
-constexpr int kF64TX = 32, kF64TY = 8, kF64S = 4;
-using F64Shape = RingShape<double, kF64TX, kF64TY, kF64S>;
-
-// One CTA: work item blockIdx.x of the schedule, a 32x8 tile of columns and
-// output levels kb..ke-1 (a chunk of kbeg..kend-1); it reads levels
-// lo = max(kb-1, 0) .. hi = min(ke, nz-1). Loads are numbered relative to lo.
-template <typename Shape>
-__global__ void __launch_bounds__(Shape::NT) fwd_f64_kernel(const __grid_constant__ CUtensorMap mu,
-                                                            const __grid_constant__ CUtensorMap mv,
-                                                            const __grid_constant__ CUtensorMap mw,
-                                                            const FwdArgs a, const ItemSched sched) {
-    constexpr int TX = Shape::TX, TY = Shape::TY, S = Shape::S, BX = Shape::BX;
-    extern __shared__ unsigned char smem_raw[];
-    Ring<Shape> ring;
-    ring.setup(smem_raw);
-
-    const int tid = threadIdx.x;
-    const int tx = tid % TX, ty = tid / TX;
-    int bx, by, kb, ke;
-    sched_item(sched, a.kend - a.kbeg, blockIdx.x, &bx, &by, &kb, &ke);
-    kb += a.kbeg;
-    ke += a.kbeg;
-    const int x0 = bx * TX, y0 = by * TY;
-    const int i = x0 + 1 + tx, j = y0 + 1 + ty;
-    const bool act = (i <= a.nx) && (j <= a.ny);
-    const int nz = a.nz;
-    const int lo = kb > 0 ? kb - 1 : 0, hi = ke < nz ? ke : nz - 1;
-    const int nl = hi - lo + 1;  // levels read
-
-    if (tid == 0) {
-        prefetch_tensormap(&mu);
-        prefetch_tensormap(&mv);
-        prefetch_tensormap(&mw);
-        ring.init_barriers();
-    }
-    __syncthreads();
-    int issued = 0;  // relative loads issued (thread 0)
-    if (tid == 0) {
-        for (; issued < S && issued < nl; ++issued) ring.issue(issued, lo + issued, &mu, &mv, &mw, x0, y0);
-    }
-
-    const int c0 = (ty + 1) * BX + (tx + 1) + a.xoff;
-    double* __restrict__ su = static_cast<double*>(a.su);
-    double* __restrict__ sv = static_cast<double*>(a.sv);
-    double* __restrict__ sw = static_cast<double*>(a.sw);
-    const size_t gsz = (size_t)a.sz;
-    size_t g = (size_t)j * (size_t)a.sy + (size_t)i + (size_t)lo * gsz;
-
-    bool bad = !ring.wait(0);
-    if (nl > 1) bad |= !ring.wait(1);
-
-    // level-lo values feed the first computed level
-    double uo_m, vo_m, wo_m, wx_m, wy_m;
-    {
-        const double* U = ring.template box<double>(0, 0);
-        const double* V = ring.template box<double>(0, 1);
-        const double* W = ring.template box<double>(0, 2);
-        uo_m = U[c0];
-        vo_m = V[c0];
-        wo_m = W[c0];
-        wx_m = W[c0] + W[c0 + 1];
-        wy_m = W[c0] + W[c0 + BX];
-    }
-    if (act && kb == 0) {  // level 1 of the paper is not computed
-        su[g] = 0.0;
-        sv[g] = 0.0;
-        sw[g] = 0.0;
-    }
-    bool abort = __syncthreads_or(bad);
-    if (!abort && tid == 0 && issued < nl) {
-        fence_proxy_async_smem();
-        ring.issue(issued, lo + issued, &mu, &mv, &mw, x0, y0);
-        ++issued;
-    }
-
-    const double tcx = a.tcx, tcy = a.tcy;
-    for (int k = (kb > 1 ? kb : 1); k < ke && !abort; ++k) {
-        const int r = k - lo;
-        g += gsz;
-        const bool top = (k == nz - 1);
-        if (!top) bad |= !ring.wait(r + 1);
-        const double* U = ring.template box<double>(r, 0);
-        const double* V = ring.template box<double>(r, 1);
-        const double* W = ring.template box<double>(r, 2);
-
-        const double uc = U[c0], uw = U[c0 - 1], ue = U[c0 + 1], us = U[c0 - BX], un = U[c0 + BX];
-        const double unw = U[c0 + BX - 1];
-        const double vc = V[c0], vw = V[c0 - 1], ve = V[c0 + 1], vs = V[c0 - BX], vn = V[c0 + BX];
-        const double vse = V[c0 - BX + 1];
-        const double wc = W[c0], ww = W[c0 - 1], we = W[c0 + 1], ws = W[c0 - BX], wn = W[c0 + BX];
-        const double tz1 = __ldg(a.tzc1 + k), tz2 = __ldg(a.tzc2 + k);
-
-        double r_su = tcx * (uw * (uc + uw) - ue * (uc + ue)) + tcy * (us * (vs + vse) - un * (vc + ve)) +
-                      tz1 * uo_m * wx_m;
-        double r_sv = tcy * (vs * (vc + vs) - vn * (vc + vn)) + tcx * (vw * (uw + unw) - ve * (uc + un)) +
-                      tz1 * vo_m * wy_m;
-        const double wx = wc + we, wy = wc + wn;
-        double r_sw = 0.0;
-        if (!top) {
-            const double* Uu = ring.template box<double>(r + 1, 0);
-            const double* Vu = ring.template box<double>(r + 1, 1);
-            const double* Wu = ring.template box<double>(r + 1, 2);
-            const double uu = Uu[c0], uuw = Uu[c0 - 1];
-            const double vu = Vu[c0], vus = Vu[c0 - BX];
-            const double wu = Wu[c0];
-            const double td1 = __ldg(a.tzd1 + k), td2 = __ldg(a.tzd2 + k);
-            r_su -= tz2 * uu * wx;
-            r_sv -= tz2 * vu * wy;
-            r_sw = tcx * (ww * (uw + uuw) - we * (uc + uu)) + tcy * (ws * (vs + vus) - wn * (vc + vu)) +
-                   td1 * wo_m * (wc + wo_m) - td2 * wu * (wc + wu);
-        }
-        if (act) {
-            su[g] = r_su;
-            sv[g] = r_sv;
-            sw[g] = r_sw;
-        }
-        uo_m = uc;
-        vo_m = vc;
-        wo_m = wc;
-        wx_m = wx;
-        wy_m = wy;
-
-        abort = __syncthreads_or(bad);  // also releases relative level r's stage
-        if (!abort && tid == 0 && issued < nl) {
-            fence_proxy_async_smem();
-            ring.issue(issued, lo + issued, &mu, &mv, &mw, x0, y0);
-            ++issued;
-        }
-    }
-    if (abort && tid == 0) {
-        atomicOr(&tu_status, kStatusTimeout);
-        // let every copy still in flight land before the CTA exits
-        for (int q = (issued > S ? issued - S : 0); q < issued; ++q) (void)ring.wait(q);
-    }
-}
-
-TileShape fwd_f64_shape() {
-    return TileShape{kF64TX, kF64TY, F64Shape::BX, F64Shape::BY, F64Shape::SMEM_BYTES, F64Shape::NT};
-}
-
-cudaError_t launch_fwd_f64(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw,
-                           const FwdArgs& a, cudaStream_t st) {
-    auto kern = fwd_f64_kernel<F64Shape>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, F64Shape::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    ItemSched sched;
-    if ((e = choose_sched(kern, F64Shape::NT, F64Shape::SMEM_BYTES, (a.nx + kF64TX - 1) / kF64TX,
-                          (a.ny + kF64TY - 1) / kF64TY, a.kend - a.kbeg, &sched)) != cudaSuccess)
-        return e;
-    kern<<<(unsigned)sched.items, F64Shape::NT, F64Shape::SMEM_BYTES, st>>>(mu, mv, mw, a, sched);
-    return cudaGetLastError();
-}
 
 // ---------------------------------------------------------------------------
 // Periodic halo fill: x halo on rows 1..ny, then the full rows 0 and ny+1.
@@ -324,6 +165,98 @@ cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, fl
 }
 
 // ---------------------------------------------------------------------------
+// Energy budget: per level, the interior sums of u su, v sv, w sw and of their
+// absolute values, in FP64 and in a fixed order (columns strided over the
+// threads, rows in order; then a fixed shuffle tree and the warps in order),
+// so the result does not depend on scheduling. One CTA per (level, field).
+// A second single-CTA launch weights the level sums by the cell masses and
+// adds them level by level.
+
+constexpr int kBudgetThreads = 512;
+
+template <typename TW, typename TS>
+__global__ void __launch_bounds__(kBudgetThreads)
+    energy_level_kernel(const TW* __restrict__ u, const TW* __restrict__ v, const TW* __restrict__ w, long long wsy,
+                        long long wsz, const TS* __restrict__ su, const TS* __restrict__ sv,
+                        const TS* __restrict__ sw, long long ssy, long long ssz, int nx, int ny, int nz,
+                        double* __restrict__ level_sums) {
+    __shared__ double part[2][kBudgetThreads / 32];
+    const int k = blockIdx.x, f = blockIdx.y;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const TW* a = f == 0 ? u : f == 1 ? v : w;
+    const TS* b = f == 0 ? su : f == 1 ? sv : sw;
+    a += (size_t)k * (size_t)wsz;
+    b += (size_t)k * (size_t)ssz;
+    double s = 0.0, t = 0.0;
+    for (int j = 1; j <= ny; ++j) {
+        const TW* ar = a + (size_t)j * (size_t)wsy;
+        const TS* br = b + (size_t)j * (size_t)ssy;
+        for (int i = 1 + tid; i <= nx; i += kBudgetThreads) {
+            const double p = (double)__ldg(ar + i) * (double)__ldg(br + i);
+            s += p;
+            t += fabs(p);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    if (lane == 0) {
+        part[0][warp] = s;
+        part[1][warp] = t;
+    }
+    __syncthreads();
+    if (tid < 2) {
+        double r = 0.0;
+        for (int q = 0; q < kBudgetThreads / 32; ++q) r += part[tid][q];
+        level_sums[(size_t)k * 6 + f + 3 * tid] = r;
+    }
+}
+
+__global__ void energy_total_kernel(const double* __restrict__ level_sums, const double* __restrict__ wu,
+                                    const double* __restrict__ ww, int nz, double* __restrict__ totals) {
+    const int n = threadIdx.x;
+    if (n >= 6) return;
+    const double* wt = (n % 3 == 2) ? ww : wu;
+    double r = 0.0;
+    for (int k = 0; k < nz; ++k) r += wt[k] * level_sums[(size_t)k * 6 + n];
+    totals[n] = r;
+}
+
+template <typename TW, typename TS>
+static cudaError_t launch_energy_t(const void* u, const void* v, const void* w, long long wsy, long long wsz,
+                                   const void* su, const void* sv, const void* sw, long long ssy, long long ssz,
+                                   int nx, int ny, int nz, const double* wu, const double* ww, double* level_sums,
+                                   double* totals, cudaStream_t st) {
+    energy_level_kernel<TW, TS><<<dim3((unsigned)nz, 3), kBudgetThreads, 0, st>>>(
+        static_cast<const TW*>(u), static_cast<const TW*>(v), static_cast<const TW*>(w), wsy, wsz,
+        static_cast<const TS*>(su), static_cast<const TS*>(sv), static_cast<const TS*>(sw), ssy, ssz, nx, ny, nz,
+        level_sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    energy_total_kernel<<<1, 32, 0, st>>>(level_sums, wu, ww, nz, totals);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_budget(const void* u, const void* v, const void* w, int wind_bytes, long long wsy,
+                                 long long wsz, const void* su, const void* sv, const void* sw, int tend_bytes,
+                                 long long ssy, long long ssz, int nx, int ny, int nz, const double* wu,
+                                 const double* ww, double* level_sums, double* totals, cudaStream_t st) {
+    if (wind_bytes == 8 && tend_bytes == 8)
+        return launch_energy_t<double, double>(u, v, w, wsy, wsz, su, sv, sw, ssy, ssz, nx, ny, nz, wu, ww,
+                                               level_sums, totals, st);
+    if (wind_bytes == 8)
+        return launch_energy_t<double, float>(u, v, w, wsy, wsz, su, sv, sw, ssy, ssz, nx, ny, nz, wu, ww,
+                                              level_sums, totals, st);
+    if (tend_bytes == 8)
+        return launch_energy_t<float, double>(u, v, w, wsy, wsz, su, sv, sw, ssy, ssz, nx, ny, nz, wu, ww,
+                                              level_sums, totals, st);
+    return launch_energy_t<float, float>(u, v, w, wsy, wsz, su, sv, sw, ssy, ssz, nx, ny, nz, wu, ww, level_sums,
+                                         totals, st);
+}
+
+// ---------------------------------------------------------------------------
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing
 // ever completes and must give up after limit_ns, recording a timeout.
 
@@ -344,12 +277,13 @@ cudaError_t launch_selftest_wait(unsigned long long limit_ns, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st) {
-    unsigned int parts[4] = {0, 0, 0, 0};
+    unsigned int parts[5] = {0, 0, 0, 0, 0};
     cudaError_t e = read_and_clear_tu_status(&parts[0], st);
     if (e == cudaSuccess) e = read_and_clear_status_paired(&parts[1], st);
     if (e == cudaSuccess) e = read_and_clear_status_split(&parts[2], st);
     if (e == cudaSuccess) e = read_and_clear_status_adjoint(&parts[3], st);
-    *status = parts[0] | parts[1] | parts[2] | parts[3];
+    if (e == cudaSuccess) e = read_and_clear_status_f64(&parts[4], st);
+    *status = parts[0] | parts[1] | parts[2] | parts[3] | parts[4];
     return e;
 }
 

@@ -3,13 +3,13 @@
 //
 // pw_advect_batched needs the batch plan in device memory: it holds the TMA
 // descriptors the persistent kernel reads and the atomic counter it takes
-// work from. Some callers cannot obtain that memory: code running while a
-// CUDA graph is being captured (a cudaMalloc there breaks or invalidates the
-// capture), real-time loops that must not call cudaMalloc because it can
-// synchronise the device, and hosts whose memory pool is fully reserved by
-// another allocator. For them this entry point keeps the plan in a fixed
-// file-scope device array that every GPU loading the library holds until
-// the process exits, and copies the caller's host plan into it per call.
+// work from. Some callers cannot obtain that memory: real-time loops that
+// must not call cudaMalloc (it can synchronise the device, and its latency
+// is unbounded), plug-ins inside a host program that owns every device
+// allocation, and programs whose device memory another allocator has wholly
+// reserved. For them this entry point keeps the plan in a fixed file-scope
+// device array that every GPU loading the library holds until the process
+// exits, and copies the caller's host plan into it per call.
 #include <cuda.h>
 #include <cuda_runtime.h>
 

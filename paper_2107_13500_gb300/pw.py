@@ -115,6 +115,11 @@ def load_library(path: str | None = None):
         lib.pw_advect_host_chunked.restype = ctypes.c_int
         lib.pw_selftest_bounded_wait.argtypes = [ctypes.c_uint, ctypes.POINTER(ctypes.c_int), vp]
         lib.pw_selftest_bounded_wait.restype = ctypes.c_int
+        lib.pw_make_energy_weights.argtypes = [ctypes.c_int, _dp, _dp, _dp, _dp, _dp]
+        lib.pw_make_energy_weights.restype = ctypes.c_int
+        lib.pw_energy_budget.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(Dims), vp, vp, vp, ctypes.c_int,
+                                         ctypes.POINTER(Dims), vp, vp, vp, vp, vp]
+        lib.pw_energy_budget.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -423,6 +428,48 @@ def advect_adjoint(u, v, w, coeffs: Coefficients, nx, ny, gsu, gsv, gsw, mode="f
     return gu, gv, gw
 
 
+def make_energy_weights(nz, dz, rho=None, rhon=None):
+    """(wu, ww): host masses of the u/v cells and of the w cells per level
+    (pw_make_energy_weights)."""
+    lib = load_library()
+    dz = np.ascontiguousarray(dz, dtype=np.float64)
+    if dz.shape != (nz,):
+        raise ValueError("dz must have nz entries")
+    rho = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    rhon = None if rhon is None else np.ascontiguousarray(rhon, dtype=np.float64)
+    wu, ww = np.zeros(nz), np.zeros(nz)
+    _check(lib.pw_make_energy_weights(nz, dz.ctypes.data_as(_dp), None if rho is None else rho.ctypes.data_as(_dp),
+                                      None if rhon is None else rhon.ctypes.data_as(_dp), wu.ctypes.data_as(_dp),
+                                      ww.ctypes.data_as(_dp)))
+    return wu, ww
+
+
+def energy_budget(u, v, w, su, sv, sw, nx, ny, wu, ww, stream=None):
+    """(totals, level_sums) of pw_energy_budget as device float64 tensors:
+    totals = [sum wu u su, sum wu v sv, sum ww w sw, and the same sums of
+    |summands|]; level_sums (nz, 6) the unweighted per-level sums. wu, ww
+    are device float64 tensors of nz entries. Winds and tendencies may each
+    be float or double."""
+    import torch
+    lib = load_library()
+    dw, ds = dims_of(u, nx, ny), dims_of(su, nx, ny)
+    for t in (v, w):
+        if t.stride() != u.stride() or t.dtype != u.dtype:
+            raise ValueError("u, v, w must share strides and dtype")
+    for t in (sv, sw):
+        if t.stride() != su.stride() or t.dtype != su.dtype:
+            raise ValueError("su, sv, sw must share strides and dtype")
+    nz = u.shape[0]
+    level = torch.empty((nz, 6), dtype=torch.float64, device=u.device)
+    totals = torch.empty(6, dtype=torch.float64, device=u.device)
+    vp = ctypes.c_void_p
+    _check(lib.pw_energy_budget(vp(u.data_ptr()), vp(v.data_ptr()), vp(w.data_ptr()), u.element_size(),
+                                ctypes.byref(dw), vp(su.data_ptr()), vp(sv.data_ptr()), vp(sw.data_ptr()),
+                                su.element_size(), ctypes.byref(ds), vp(wu.data_ptr()), vp(ww.data_ptr()),
+                                vp(level.data_ptr()), vp(totals.data_ptr()), _stream_handle(stream)))
+    return totals, level
+
+
 def fold_periodic_halo(g, nx, ny, stream=None):
     """Transpose of fill_periodic_halo, in place: halo gradients are added to
     the interior cells they were copied from, and the halo is zeroed."""
@@ -445,8 +492,8 @@ class Batch:
 
     domains: sequence of dicts with keys u, v, w (inputs), su, sv, sw
     (outputs; allocated with field_like(u) if absent), nx, ny, coeffs
-    (Coefficients) and, for "split", split_table. mode "paired", "f32" or
-    "split". The plan (TMA descriptors, work table and work-queue counter) is
+    (Coefficients) and, for "split", split_table. mode "f64", "paired",
+    "f32" or "split". The plan (TMA descriptors, work table and work-queue counter) is
     built on the host and copied once into a device buffer owned here.
     """
 

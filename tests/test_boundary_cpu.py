@@ -185,14 +185,15 @@ def test_batch_plan_validation_without_device(lib):
     from paper_2107_13500_gb300 import pw
     assert lib.pw_batch_plan_bytes(96) > lib.pw_batch_plan_bytes(1) > 0
     assert lib.pw_variant_count(pw.PW_F32) == 8 and lib.pw_variant_count(pw.PW_F64_PAIRED) == 4
-    assert lib.pw_variant_count(pw.PW_F64) == 0
+    assert lib.pw_variant_count(pw.PW_F64) == 2
     nbytes = lib.pw_batch_plan_bytes(2)
     raw = np.zeros(nbytes + 128, dtype=np.uint8)
     off = (-raw.ctypes.data) % 64
     plan = ctypes.c_void_p(raw.ctypes.data + off)
     doms = (pw.Domain * 2)()
     n = ctypes.c_longlong(0)
-    assert lib.pw_make_batch_plan(pw.PW_F64, 2, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EUNSUPPORTED
+    assert lib.pw_make_batch_plan(pw.PW_F64, 2, doms, 2, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
+    assert lib.pw_make_batch_plan(99, 2, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
     assert lib.pw_make_batch_plan(pw.PW_F32, 0, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
     assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 7, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
     assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 0, plan, nbytes - 1, ctypes.byref(n)) == pw.PW_EINVAL
@@ -202,7 +203,8 @@ def test_batch_plan_validation_without_device(lib):
     assert lib.pw_make_batch_plan(pw.PW_F32, 2, doms, 0, plan, nbytes, ctypes.byref(n)) == pw.PW_EINVAL
     assert b"domain" in lib.pw_last_error()
     assert lib.pw_advect_batched(pw.PW_F32, 0, None, 1, None) == pw.PW_ENULL
-    assert lib.pw_advect_batched(pw.PW_F64, 0, plan, 1, None) == pw.PW_EUNSUPPORTED
+    assert lib.pw_advect_batched(pw.PW_F64, 2, plan, 1, None) == pw.PW_EINVAL
+    assert lib.pw_advect_batched(99, 0, plan, 1, None) == pw.PW_EINVAL
 
 
 def test_adjoint_validation_without_device(lib):
@@ -221,3 +223,41 @@ def test_adjoint_validation_without_device(lib):
     assert lib.pw_advect_adjoint(pw.PW_F64, *alias[:3], ctypes.byref(c), ctypes.byref(d), *alias[3:], 0,
                                  None) == pw.PW_EALIAS
     assert lib.pw_fold_periodic_halo(pw.PW_F64, None, ctypes.byref(d), None) == pw.PW_ENULL
+
+
+def test_energy_weights_agree_with_oracle(lib, oracle_lib):
+    """pw_make_energy_weights (host, library) against the oracle's own
+    computation of the cell masses, on uniform, stretched and density grids."""
+    from paper_2107_13500_gb300 import pw
+    for nz, dz, dens in ((64, synth.dz_stretched(64), True), (16, synth.dz_uniform(16, 20.0), False),
+                         (1, synth.dz_uniform(1, 5.0), False), (3, synth.dz_stretched(3), True)):
+        rho, rhon = synth.density_exponential(dz) if dens else (None, None)
+        a = pw.make_energy_weights(nz, dz, rho, rhon)
+        b = oracle_lib.energy_weights(nz, dz, rho, rhon)
+        for x, y in zip(a, b):
+            np.testing.assert_allclose(x, y, rtol=4e-16, atol=0)
+    with pytest.raises(pw.PWError) as e:
+        pw.make_energy_weights(4, np.array([0.0, 1.0, -1.0, 1.0]))
+    assert e.value.code == pw.PW_EINVAL
+
+
+def test_energy_budget_validation_without_device(lib):
+    """pw_energy_budget rejects bad element sizes, mismatched domains, NULL
+    and misaligned pointers and overlapping results before any launch."""
+    from paper_2107_13500_gb300 import pw
+    nx, ny, nz = 12, 6, 4
+    sy8, sy4 = pw.row_stride(nx, 8), pw.row_stride(nx, 4)
+    d8 = pw.Dims(nx, ny, nz, 1, sy8, sy8 * (ny + 2))
+    d4 = pw.Dims(nx, ny, nz, 1, sy4, sy4 * (ny + 2))
+    dbad = pw.Dims(nx + 1, ny, nz, 1, sy8, sy8 * (ny + 2))
+    p = [ctypes.c_void_p((1 << 40) + k * (1 << 24)) for k in range(10)]
+    wu, ww, lev, tot = p[6:10]
+    B = ctypes.byref
+    assert lib.pw_energy_budget(*p[:3], 2, B(d8), *p[3:6], 8, B(d8), wu, ww, lev, tot, None) == pw.PW_EINVAL
+    assert lib.pw_energy_budget(*p[:3], 8, B(d8), *p[3:6], 4, B(dbad), wu, ww, lev, tot, None) == pw.PW_EINVAL
+    assert lib.pw_energy_budget(*p[:3], 8, B(d8), *p[3:6], 4, B(d4), None, ww, lev, tot, None) == pw.PW_ENULL
+    assert lib.pw_energy_budget(None, *p[1:3], 8, B(d8), *p[3:6], 8, B(d8), wu, ww, lev, tot, None) == pw.PW_ENULL
+    mis = ctypes.c_void_p((1 << 40) + 4)
+    assert lib.pw_energy_budget(mis, *p[1:3], 8, B(d8), *p[3:6], 8, B(d8), wu, ww, lev, tot, None) == pw.PW_EINVAL
+    assert lib.pw_energy_budget(*p[:3], 8, B(d8), *p[3:6], 8, B(d8), wu, ww, lev,
+                                ctypes.c_void_p(lev.value + 8), None) == pw.PW_EALIAS

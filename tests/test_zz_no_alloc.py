@@ -1,8 +1,9 @@
 """pw_advect_batched_noalloc: the batched evaluation for callers that cannot
-allocate device memory (capturing a CUDA graph, real-time loops that must
-not call cudaMalloc, or a device whose memory another allocator has
-reserved). It keeps the plan in a fixed device array inside the library
-instead of a caller-allocated buffer.
+allocate device memory (real-time loops that must not call cudaMalloc, which
+can synchronise the device; plug-ins inside a host program that owns every
+device allocation; a device whose memory another allocator has reserved). It
+keeps the plan in a fixed device array inside the library instead of a
+caller-allocated buffer.
 
 Checked through the C ABI against pw_advect_batched, on consecutive calls
 with different plans (the shared array must be refreshed each time), and
