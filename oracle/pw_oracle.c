@@ -311,29 +311,49 @@ int pwo_energy_weights(int nz, const double *dz, const double *rho, const double
 /*
  * Energy budget: out[0..2] = sum over the interior of wu(k) u su, wu(k) v sv
  * and ww(k) w sw; out[3..5] = the same sums of absolute values. Levels in
- * order, rows in order, columns in order, one FP64 accumulator per sum.
+ * order, rows in order, columns in order. Each sum is accumulated with
+ * Neumaier's compensated summation (Kahan's method with the Babuska /
+ * Neumaier branch on magnitudes), so its error stays near one rounding of
+ * the result whatever the number of summands.
  */
+typedef struct {
+    double s, c;  /* running sum and its compensation */
+} csum;
+
+static void csum_add(csum *a, double x)
+{
+    const double t = a->s + x;
+    if (absd(a->s) >= absd(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+
 void pwo_energy_budget(int nx, int ny, int nz, long long sy, long long sz,
                        const double *u, const double *v, const double *w,
                        const double *su, const double *sv, const double *sw,
                        const double *wu, const double *ww, double *out)
 {
-    for (int n = 0; n < 6; ++n) out[n] = 0.0;
+    csum acc[6];
+    for (int n = 0; n < 6; ++n) {
+        acc[n].s = 0.0;
+        acc[n].c = 0.0;
+    }
     for (int k = 0; k < nz; ++k) {
         for (int j = 1; j <= ny; ++j) {
             for (int i = 1; i <= nx; ++i) {
                 const double eu = wu[k] * AT(u, k, j, i) * AT(su, k, j, i);
                 const double ev = wu[k] * AT(v, k, j, i) * AT(sv, k, j, i);
                 const double ew = ww[k] * AT(w, k, j, i) * AT(sw, k, j, i);
-                out[0] += eu;
-                out[1] += ev;
-                out[2] += ew;
-                out[3] += absd(eu);
-                out[4] += absd(ev);
-                out[5] += absd(ew);
+                csum_add(&acc[0], eu);
+                csum_add(&acc[1], ev);
+                csum_add(&acc[2], ew);
+                csum_add(&acc[3], absd(eu));
+                csum_add(&acc[4], absd(ev));
+                csum_add(&acc[5], absd(ew));
             }
         }
     }
+    for (int n = 0; n < 6; ++n) out[n] = acc[n].s + acc[n].c;
 }
 
 /*

@@ -68,7 +68,8 @@ int pwo_energy_weights(int nz, const double *dz, const double *rho, const double
 
 /* out[0..2] = sum over the interior of wu(k)*u*su, wu(k)*v*sv, ww(k)*w*sw;
  * out[3..5] = the sums of the absolute values of the same summands. Fixed
- * order (levels, rows, columns), one FP64 accumulator each. */
+ * order (levels, rows, columns); each sum compensated (Neumaier), so its
+ * error does not grow with the number of summands. */
 void pwo_energy_budget(int nx, int ny, int nz, long long sy, long long sz,
                        const double *u, const double *v, const double *w,
                        const double *su, const double *sv, const double *sw,

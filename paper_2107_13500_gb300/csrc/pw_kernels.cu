@@ -10,6 +10,7 @@
 
 #include "pw_common.cuh"
 #include "pw_internal.h"
+#include "pw_pair.cuh"
 #include "pw_ring.cuh"
 
 namespace pw {
@@ -55,31 +56,66 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 }
 
 // ---------------------------------------------------------------------------
-// Per-level mean and float perturbation, in two launches.
+// Per-level mean and float perturbation, in two launches, kept off the slow
+// FP64 pipe (about two FP64 lane operations per clock per SM on GB300) so
+// that both are bound by HBM.
 //
 // split_mean_kernel: a cluster of kSplitCluster CTAs takes one level. Each
-// CTA sums its share of the interior rows in FP64 (each thread a fixed set of
-// columns, rows in order; then a fixed shuffle tree per warp and the warps in
-// order), and rank 0 adds the cluster's partial sums in rank order through
-// distributed shared memory. The result does not depend on scheduling.
+// thread sums its share of the interior (a fixed set of columns, rows in
+// order) in paired FP32 -- each double split into a float pair by integer
+// operations, pairs added with TwoSum -- then a fixed shuffle tree per warp,
+// the warps in order, and rank 0 adds the cluster's partial sums in rank
+// order through distributed shared memory, so the mean does not depend on
+// scheduling. A level holding a nonzero magnitude outside [2^-60, 2^100), an
+// infinity or a NaN is summed again in FP64 by the same cluster (same fixed
+// order), since float pairs cannot carry it.
 //
 // split_pert_kernel: a flat grid over every cell (halo included) writes
-// float(f - mean[k]).
-//
-// A single launch that kept each level's clusters on it for both passes was
-// slower: with one cluster per level resident at a time the grid is too small
-// to load every SM's FP64 pipe, and with all levels resident the second pass
-// re-reads the field from HBM anyway. Both kernels are bound by the FP64
-// pipe (one add per cell each).
+// float(f - mean[k]): one FP64 subtraction, then the round-to-nearest-even
+// conversion to float by integer operations (the hardware conversion issues
+// on the FP64 pipe too), which gives the hardware's result bit for bit; the
+// values outside the normal float range take the hardware conversion. The
+// levels are walked top down, the reverse of the mean pass, so the levels
+// that pass read last are read again while they are still in L2.
 
 constexpr int kSplitThreads = 256, kSplitCluster = 8, kSplitUnroll = 8;
 constexpr int kPertThreads = 128, kPertRows = 8;  // columns per CTA, rows per thread
 
+// Biased double exponents of the magnitudes the paired sum carries: [2^-60, 2^100).
+constexpr unsigned kPairExpLo = 1023 - 60, kPairExpHi = 1023 + 100;
+
+__device__ __forceinline__ bool pair_summable(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
+    return (b << 1) == 0 || (e - kPairExpLo < kPairExpHi - kPairExpLo);
+}
+
+// double -> float rounded to nearest even. Results in the normal float range
+// and zeros by integer operations; everything else (float subnormals,
+// overflow from below 2^128 excepted, infinities, NaN) by the hardware.
+__device__ __forceinline__ float double_to_float_rn(double d) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const unsigned e = (hi >> 20) & 0x7FFu;  // biased double exponent
+    if (e - 897u < 254u) {                  // float exponent 1..254
+        const unsigned m = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;  // the 23 fraction bits kept
+        const unsigned rem = lo & 0x1FFFFFFFu;                       // the 29 dropped
+        const unsigned inc = (rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u));
+        // a carry out of the fraction moves to the exponent (254 -> 255: infinity)
+        return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + m + inc));
+    }
+    if ((b << 1) == 0) return __uint_as_float(hi & 0x80000000u);
+    return __double2float_rn(d);
+}
+
 __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitThreads)
     split_mean_kernel(const double* __restrict__ f, long long fsy, long long fsz, int nx, int ny, int nz,
                       double* __restrict__ mean) {
-    __shared__ double warp_part[kSplitThreads / 32];
-    __shared__ double cta_sum;
+    __shared__ float2 warp_part[kSplitThreads / 32];
+    __shared__ double warp_part64[kSplitThreads / 32];
+    __shared__ float2 cta_sum;
+    __shared__ double cta_sum64;
+    __shared__ int cta_ok;
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -89,7 +125,8 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
     // the whole cluster walks the same levels
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
         const double* lev = f + (size_t)k * (size_t)fsz;
-        double s = 0.0;
+        pf s = {0.0f, 0.0f};
+        bool ok = true;
         for (int i = 1 + tid; i <= nx; i += kSplitThreads) {
             const double* col = lev + i;
             int j = r0;
@@ -98,24 +135,62 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
 #pragma unroll
                 for (int q = 0; q < kSplitUnroll; ++q) x[q] = __ldg(col + (size_t)(j + q) * (size_t)fsy);
 #pragma unroll
-                for (int q = 0; q < kSplitUnroll; ++q) s += x[q];
+                for (int q = 0; q < kSplitUnroll; ++q) {
+                    ok &= pair_summable(x[q]);
+                    s = padd(s, split_double(x[q]));
+                }
             }
-            for (; j < r1; ++j) s += __ldg(col + (size_t)j * (size_t)fsy);
+            for (; j < r1; ++j) {
+                const double x = __ldg(col + (size_t)j * (size_t)fsy);
+                ok &= pair_summable(x);
+                s = padd(s, split_double(x));
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) warp_part[warp] = s;
-        __syncthreads();
-        if (tid == 0) {
-            double t = 0.0;
-            for (int q = 0; q < kSplitThreads / 32; ++q) t += warp_part[q];
-            cta_sum = t;
+        for (int o = 16; o > 0; o >>= 1) {
+            const pf t = {__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
+            s = padd(s, t);
         }
-        cluster.sync();  // every CTA's partial sum is in place
-        if (rank == 0 && tid == 0) {
-            double t = 0.0;
-            for (int q = 0; q < kSplitCluster; ++q) t += *cluster.map_shared_rank(&cta_sum, q);
-            mean[k] = t / ((double)nx * (double)ny);
+        if (lane == 0) warp_part[warp] = make_float2(s.h, s.l);
+        const int all_ok = __syncthreads_and(ok);
+        if (tid == 0) {
+            pf t = {0.0f, 0.0f};
+            for (int q = 0; q < kSplitThreads / 32; ++q) t = padd(t, pf{warp_part[q].x, warp_part[q].y});
+            cta_sum = make_float2(t.h, t.l);
+            cta_ok = all_ok;
+        }
+        cluster.sync();  // every CTA's partial sum and flag is in place
+        bool level_ok = true;
+        for (int q = 0; q < kSplitCluster; ++q) level_ok &= (*cluster.map_shared_rank(&cta_ok, q) != 0);
+        if (level_ok) {
+            if (rank == 0 && tid == 0) {
+                pf t = {0.0f, 0.0f};
+                for (int q = 0; q < kSplitCluster; ++q) {
+                    const float2 c = *cluster.map_shared_rank(&cta_sum, q);
+                    t = padd(t, pf{c.x, c.y});
+                }
+                mean[k] = ((double)t.h + (double)t.l) / ((double)nx * (double)ny);
+            }
+        } else {
+            // values the pairs cannot carry: the level in FP64, same order
+            double s64 = 0.0;
+            for (int i = 1 + tid; i <= nx; i += kSplitThreads)
+                for (int j = r0; j < r1; ++j) s64 += __ldg(lev + i + (size_t)j * (size_t)fsy);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+            if (lane == 0) warp_part64[warp] = s64;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int q = 0; q < kSplitThreads / 32; ++q) t += warp_part64[q];
+                cta_sum64 = t;
+            }
+            cluster.sync();
+            if (rank == 0 && tid == 0) {
+                double t = 0.0;
+                for (int q = 0; q < kSplitCluster; ++q) t += *cluster.map_shared_rank(&cta_sum64, q);
+                mean[k] = t / ((double)nx * (double)ny);
+            }
         }
         // rank 0 has read every partial sum before any CTA rewrites its own
         // (next level) or leaves
@@ -124,14 +199,14 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
 }
 
 // Thread x of CTA (bx, by, bz) converts column bx*kPertThreads + x of the
-// row chunks by, by + gridDim.y, ... (kPertRows rows each) of levels bz,
-// bz + gridDim.z, ...
+// row chunks by, by + gridDim.y, ... (kPertRows rows each) of levels
+// nz-1-bz, nz-1-bz-gridDim.z, ... (top down).
 __global__ void __launch_bounds__(kPertThreads)
     split_pert_kernel(const double* __restrict__ f, long long fsy, long long fsz, float* __restrict__ fp,
                       long long psy, long long psz, int nx, int ny, int nz, const double* __restrict__ mean) {
     const int i = blockIdx.x * kPertThreads + threadIdx.x;
     if (i > nx + 1) return;
-    for (int k = blockIdx.z; k < nz; k += gridDim.z) {
+    for (int k = nz - 1 - (int)blockIdx.z; k >= 0; k -= (int)gridDim.z) {
         const double m = __ldg(mean + k);
         for (int j0 = blockIdx.y * kPertRows; j0 < ny + 2; j0 += gridDim.y * kPertRows) {
             const double* col = f + (size_t)k * (size_t)fsz + (size_t)j0 * (size_t)fsy + i;
@@ -142,10 +217,12 @@ __global__ void __launch_bounds__(kPertThreads)
 #pragma unroll
                 for (int q = 0; q < kPertRows; ++q) x[q] = __ldg(col + (size_t)q * (size_t)fsy);
 #pragma unroll
-                for (int q = 0; q < kPertRows; ++q) ocol[(size_t)q * (size_t)psy] = (float)(x[q] - m);
+                for (int q = 0; q < kPertRows; ++q)
+                    ocol[(size_t)q * (size_t)psy] = double_to_float_rn(__dsub_rn(x[q], m));
             } else {
                 for (int q = 0; q < nr; ++q)
-                    ocol[(size_t)q * (size_t)psy] = (float)(__ldg(col + (size_t)q * (size_t)fsy) - m);
+                    ocol[(size_t)q * (size_t)psy] =
+                        double_to_float_rn(__dsub_rn(__ldg(col + (size_t)q * (size_t)fsy), m));
             }
         }
     }

@@ -122,21 +122,52 @@ def test_split_guard_bands_and_halo_untouched(gpu, aligned):
 
 
 def test_split_field_means_and_perturbations(gpu):
-    """pw_split_field: FP64 level means of the interior and float
-    perturbations on every cell, halo included."""
+    """pw_split_field: level means of the interior and float perturbations
+    on every cell, halo included. The means are summed in paired FP32 (each
+    double split into a float pair of 48 significant bits, pairs added with
+    TwoSum): each of the at most n_add additions on a thread's path (its own
+    cells, the warp tree, the warps, the cluster) errs by at most 2^-47 of
+    the magnitudes summed so far, so |mean - exact| <= n_add 2^-47 mean|f|."""
     from paper_2107_13500_gb300 import pw
     torch = gpu
-    nx, ny, nz = 70, 33, 6
-    u, _, _ = synth.fields_modes(nx, ny, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0), seed=8)
+    for nx, ny, nz in ((70, 33, 6), (512, 512, 4)):
+        u, _, _ = synth.fields_modes(nx, ny, nz, 50.0, 50.0, synth.dz_uniform(nz, 20.0), seed=8)
+        t = to_device(u, nx, torch.float64)
+        fp, mean = pw.split_field(t, nx, ny)
+        torch.cuda.synchronize()
+        m = mean.cpu().numpy()
+        inner = interior(u, nx, ny)
+        want = inner.mean(axis=(1, 2))
+        per_thread = -(-nx // 256) * -(-ny // 8)
+        n_add = per_thread + 5 + 8 + 8 + 2
+        bound = n_add * 2.0 ** -47 * np.abs(inner).mean(axis=(1, 2))
+        assert np.all(np.abs(m - want) <= bound), (np.abs(m - want) / bound)
+        p = fp.cpu().numpy()[:, :, : nx + 2].astype(np.float64)
+        exact = u[:, :, : nx + 2] - m[:, None, None]
+        assert np.all(np.abs(p - exact) <= 2.0 ** -24 * np.abs(exact) + 1e-30)
+
+
+def test_split_field_means_repeat_and_fall_back_to_fp64(gpu):
+    """The means are bit-identical from call to call (fixed summation
+    order). A level holding values the float pairs cannot carry (1e120, a
+    tiny 1e-30 among O(1) values) is summed in FP64 instead: its mean then
+    matches the FP64 average to FP64 rounding."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 300, 40, 5
+    u = synth.fields_iid(nx, ny, nz, seed=21)[0]
+    u[2, 5, 7] = 1e120
+    u[3, 9, 11] = 1e-30
     t = to_device(u, nx, torch.float64)
-    fp, mean = pw.split_field(t, nx, ny)
+    runs = [pw.split_field(t, nx, ny)[1].clone() for _ in range(3)]
     torch.cuda.synchronize()
-    m = mean.cpu().numpy()
-    want = interior(u, nx, ny).mean(axis=(1, 2))
-    np.testing.assert_allclose(m, want, rtol=1e-14, atol=1e-14)
-    p = fp.cpu().numpy()[:, :, : nx + 2].astype(np.float64)
-    exact = u[:, :, : nx + 2] - m[:, None, None]
-    assert np.all(np.abs(p - exact) <= 2.0 ** -24 * np.abs(exact) + 1e-30)
+    for r in runs[1:]:
+        assert torch.equal(r.view(torch.int64), runs[0].view(torch.int64))
+    m = runs[0].cpu().numpy()
+    inner = interior(u, nx, ny)
+    want = inner.mean(axis=(1, 2))
+    scale = np.abs(inner).mean(axis=(1, 2))
+    assert np.all(np.abs(m[2:4] - want[2:4]) <= 1e-13 * scale[2:4]), (m[2:4], want[2:4])
 
 
 @pytest.mark.parametrize("nz", [5, 40])
