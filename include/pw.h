@@ -115,11 +115,19 @@ int pw_fill_periodic_halo(pw_dtype dtype, void *field, const pw_dims *dims, void
  * Unlisted indices are (k, j, i). All of u, v, w, su, sv, sw share `dims`.
  *
  * dtype PW_F64 / PW_F64_PAIRED: u, v, w, su, sv, sw are double; split must
- *   be NULL. PAIRED carries every value as an unevaluated sum of two floats
- *   (about 48 significant bits); its error at each point stays within 1e-13
- *   of the sum of the absolute values of the monomials c*x*y of the formula
- *   (each flux c*x*(y+z) counting |c||x|(|y|+|z|)), for inputs and
- *   coefficients whose magnitudes lie in [2^-60, 2^60] (or are 0).
+ *   be NULL. Error scales at a point: A = sum over the face terms c*q*(a+b)
+ *   of |c||q||a+b| (the absolute values of the products the formula adds);
+ *   M = the same with |a|+|b| in place of |a+b| (M >= A).
+ *   PW_F64 computes in FP64, each operation rounded once (u and v are scaled
+ *   by tcx and tcy once per cell, then every face sum is formed once and
+ *   shared); its error is a few units of 2^-53 of M, within 1e-13 of A.
+ *   PW_F64_PAIRED carries every value as an unevaluated sum of two floats
+ *   (about 48 significant bits); each double is split into a pair before
+ *   a + b is formed, so its error is bounded by M: within 1e-13 of M at
+ *   every point and 1e-13 of max|su| normwise. Float pairs have FP32's
+ *   exponent range: the bound holds while every input lies in
+ *   [2^-74, 2^120] (or is 0) and every product c*q*a of the formula in
+ *   [2^-100, 2^120] (tested with the winds scaled by 2^-40 and 2^40).
  * dtype PW_F32_SPLIT: u, v, w are float perturbations u' = u - U(k) about
  *   per-level means, su, sv, sw are float, and `split` is a DEVICE table of
  *   PW_SPLIT_NCOEF*nz floats built by pw_make_split_table (the coefficient
@@ -149,10 +157,16 @@ int pw_make_split_table(int nz, double tcx, double tcy, const double *tz4_host,
 
 /*
  * pw_split_field -- per-level mean and float perturbation of a double field
- * on the device: mean[k] = average of f over the interior of level k
- * (FP64, fixed summation order, so repeatable), fp = float(f - mean[k]) on
- * every cell of the level including the halo. f uses dims_f (double), fp
- * uses dims_p (float; same nx, ny, nz). mean is a DEVICE array of nz doubles.
+ * on the device: mean[k] = average of f over the interior of level k, and
+ * fp = float(f - mean[k]) on every cell of the level including the halo
+ * (the FP64 difference rounded to nearest even, bit for bit the hardware's
+ * conversion). The means are summed in a fixed order, so they repeat from
+ * call to call: in paired FP32 (about 48 significant bits; error at most a
+ * few hundred units of 2^-48 of the mean magnitude) when every interior
+ * value is 0 or lies in [2^-60, 2^100), else in FP64. Any value near the
+ * average serves the split, since pw_make_split_table and the
+ * perturbations use the same stored mean. f uses dims_f (double), fp uses
+ * dims_p (float; same nx, ny, nz). mean is a DEVICE array of nz doubles.
  * Errors: PW_ENULL, PW_EINVAL, PW_EALIAS, PW_ECUDA.
  */
 int pw_split_field(const double *f, const pw_dims *dims_f, float *fp, const pw_dims *dims_p,
