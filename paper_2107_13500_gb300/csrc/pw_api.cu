@@ -472,6 +472,10 @@ extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, c
     a.gv = gv;
     a.gw = gw;
     a.accumulate = accumulate ? 1 : 0;
+    a.vec = ((uintptr_t)gu % 16 == (uintptr_t)u % 16 && (uintptr_t)gv % 16 == (uintptr_t)u % 16 &&
+             (uintptr_t)gw % 16 == (uintptr_t)u % 16)
+                ? 1
+                : 0;
     cudaError_t e = dtype == PW_F64_PAIRED ? pw::launch_adjoint_paired(maps, a, static_cast<cudaStream_t>(stream))
                                            : pw::launch_adjoint(maps, es, a, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, who);

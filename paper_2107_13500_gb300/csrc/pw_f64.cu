@@ -409,11 +409,16 @@ int f64_variant_count() { return 2; }
 
 TileShape fwd_f64_shape_variant(int v) { return v == 1 ? f64_shape_of<FV1>() : f64_shape_of<FV0>(); }
 
-TileShape fwd_f64_shape() { return fwd_f64_shape_variant(0); }
+// Tile of the one-shot launch (pw_advect): variant 0 (32 x 16) unless built otherwise.
+#ifndef PW_F64_ONESHOT_VARIANT
+#define PW_F64_ONESHOT_VARIANT 0
+#endif
+
+TileShape fwd_f64_shape() { return fwd_f64_shape_variant(PW_F64_ONESHOT_VARIANT); }
 
 cudaError_t launch_fwd_f64(const CUtensorMap& mu, const CUtensorMap& mv, const CUtensorMap& mw, const FwdArgs& a,
                            cudaStream_t st) {
-    return launch_one<FV0>(mu, mv, mw, a, st);
+    return PW_F64_ONESHOT_VARIANT == 1 ? launch_one<FV1>(mu, mv, mw, a, st) : launch_one<FV0>(mu, mv, mw, a, st);
 }
 
 cudaError_t launch_f64_batched(int v, BatchPlan* plan, long long n_items, cudaStream_t st) {

@@ -280,6 +280,7 @@ struct AdjArgs {
     const double *tzc1, *tzc2, *tzd1, *tzd2;
     void *gu, *gv, *gw;
     int accumulate;
+    int vec;                   // gu, gv, gw have u's address modulo 16 bytes (16-byte stores of strips)
 };
 
 TileShape adjoint_shape(int elem_bytes);

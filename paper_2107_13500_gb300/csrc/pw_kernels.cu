@@ -84,18 +84,21 @@ constexpr int kPertThreads = 128, kPertRows = 8;  // columns per CTA, rows per t
 // Biased double exponents of the magnitudes the paired sum carries: [2^-60, 2^100).
 constexpr unsigned kPairExpLo = 1023 - 60, kPairExpHi = 1023 + 100;
 
+// The tests below read the two 32-bit words of a double and use integer
+// operations only: written on the 64-bit pattern, the compiler may turn an
+// exponent window or a zero test back into FP64 comparisons, which issue on
+// the slow FP64 pipe.
 __device__ __forceinline__ bool pair_summable(double x) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const unsigned e = static_cast<unsigned>(b >> 52) & 0x7FFu;
-    return (b << 1) == 0 || (e - kPairExpLo < kPairExpHi - kPairExpLo);
+    const unsigned hw = static_cast<unsigned>(__double2hiint(x)), lw = static_cast<unsigned>(__double2loint(x));
+    const unsigned e = (hw >> 20) & 0x7FFu;
+    return ((hw << 1) | lw) == 0 || (e - kPairExpLo < kPairExpHi - kPairExpLo);
 }
 
 // double -> float rounded to nearest even. Results in the normal float range
 // and zeros by integer operations; everything else (float subnormals,
 // overflow from below 2^128 excepted, infinities, NaN) by the hardware.
 __device__ __forceinline__ float double_to_float_rn(double d) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
-    const unsigned hi = static_cast<unsigned>(b >> 32), lo = static_cast<unsigned>(b);
+    const unsigned hi = static_cast<unsigned>(__double2hiint(d)), lo = static_cast<unsigned>(__double2loint(d));
     const unsigned e = (hi >> 20) & 0x7FFu;  // biased double exponent
     if (e - 897u < 254u) {                  // float exponent 1..254
         const unsigned m = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;  // the 23 fraction bits kept
@@ -104,7 +107,7 @@ __device__ __forceinline__ float double_to_float_rn(double d) {
         // a carry out of the fraction moves to the exponent (254 -> 255: infinity)
         return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + m + inc));
     }
-    if ((b << 1) == 0) return __uint_as_float(hi & 0x80000000u);
+    if (((hi << 1) | lo) == 0) return __uint_as_float(hi & 0x80000000u);
     return __double2float_rn(d);
 }
 
@@ -128,12 +131,17 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
         pf s = {0.0f, 0.0f};
         bool ok = true;
         for (int i = 1 + tid; i <= nx; i += kSplitThreads) {
-            const double* col = lev + i;
+            // rows advance by adding the stride: 64-bit integer products
+            // would issue on the FP64 pipe
+            const double* p = lev + i + (size_t)r0 * (size_t)fsy;
             int j = r0;
             for (; j + kSplitUnroll <= r1; j += kSplitUnroll) {
                 double x[kSplitUnroll];
 #pragma unroll
-                for (int q = 0; q < kSplitUnroll; ++q) x[q] = __ldg(col + (size_t)(j + q) * (size_t)fsy);
+                for (int q = 0; q < kSplitUnroll; ++q) {
+                    x[q] = __ldg(p);
+                    p += fsy;
+                }
 #pragma unroll
                 for (int q = 0; q < kSplitUnroll; ++q) {
                     ok &= pair_summable(x[q]);
@@ -141,7 +149,8 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
                 }
             }
             for (; j < r1; ++j) {
-                const double x = __ldg(col + (size_t)j * (size_t)fsy);
+                const double x = __ldg(p);
+                p += fsy;
                 ok &= pair_summable(x);
                 s = padd(s, split_double(x));
             }
@@ -174,8 +183,10 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
         } else {
             // values the pairs cannot carry: the level in FP64, same order
             double s64 = 0.0;
-            for (int i = 1 + tid; i <= nx; i += kSplitThreads)
-                for (int j = r0; j < r1; ++j) s64 += __ldg(lev + i + (size_t)j * (size_t)fsy);
+            for (int i = 1 + tid; i <= nx; i += kSplitThreads) {
+                const double* p = lev + i + (size_t)r0 * (size_t)fsy;
+                for (int j = r0; j < r1; ++j, p += fsy) s64 += __ldg(p);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
             if (lane == 0) warp_part64[warp] = s64;
@@ -215,14 +226,17 @@ __global__ void __launch_bounds__(kPertThreads)
             if (nr == kPertRows) {
                 double x[kPertRows];
 #pragma unroll
-                for (int q = 0; q < kPertRows; ++q) x[q] = __ldg(col + (size_t)q * (size_t)fsy);
+                for (int q = 0; q < kPertRows; ++q) {
+                    x[q] = __ldg(col);
+                    col += fsy;
+                }
 #pragma unroll
-                for (int q = 0; q < kPertRows; ++q)
-                    ocol[(size_t)q * (size_t)psy] = double_to_float_rn(__dsub_rn(x[q], m));
+                for (int q = 0; q < kPertRows; ++q) {
+                    *ocol = double_to_float_rn(__dsub_rn(x[q], m));
+                    ocol += psy;
+                }
             } else {
-                for (int q = 0; q < nr; ++q)
-                    ocol[(size_t)q * (size_t)psy] =
-                        double_to_float_rn(__dsub_rn(__ldg(col + (size_t)q * (size_t)fsy), m));
+                for (int q = 0; q < nr; ++q, col += fsy, ocol += psy) *ocol = double_to_float_rn(__dsub_rn(__ldg(col), m));
             }
         }
     }
@@ -265,9 +279,9 @@ __global__ void __launch_bounds__(kBudgetThreads)
     a += (size_t)k * (size_t)wsz;
     b += (size_t)k * (size_t)ssz;
     double s = 0.0, t = 0.0;
-    for (int j = 1; j <= ny; ++j) {
-        const TW* ar = a + (size_t)j * (size_t)wsy;
-        const TS* br = b + (size_t)j * (size_t)ssy;
+    const TW* ar = a + wsy;  // row j = 1; rows advance by adding the stride
+    const TS* br = b + ssy;
+    for (int j = 1; j <= ny; ++j, ar += wsy, br += ssy) {
         for (int i = 1 + tid; i <= nx; i += kBudgetThreads) {
             const double p = (double)__ldg(ar + i) * (double)__ldg(br + i);
             s += p;
