@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libpw.so")
 OBJ_DIR = os.path.join(PKG, "_build")
 
-SOURCES = ["pw_api.cu", "pw_kernels.cu", "pw_f64.cu", "pw_paired.cu", "pw_split.cu", "pw_adjoint.cu", "pw_noalloc.cu"]
+SOURCES = ["pw_api.cu", "pw_kernels.cu", "pw_f64.cu", "pw_paired.cu", "pw_split.cu", "pw_adjoint.cu", "pw_adjoint_f64.cu", "pw_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

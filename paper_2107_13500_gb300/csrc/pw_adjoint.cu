@@ -1,5 +1,7 @@
-// pw_adjoint.cu -- transpose of the PW advection Jacobian (gather form), and
-// the transpose of the periodic halo fill.
+// pw_adjoint.cu -- transpose of the PW advection Jacobian in paired FP32
+// (PW_F64_PAIRED) and FP32 (PW_F32), cell by cell (gather form), and the
+// transpose of the periodic halo fill. (Native FP64 is in pw_adjoint_f64.cu,
+// regrouped by faces.)
 //
 // The forward map is a quadratic form: every term is c * p * (q + r) with c a
 // coefficient and p, q, r field values, so its partial derivatives are
@@ -8,14 +10,14 @@
 // that derivative. Writing each forward term out (su: T1..T6, sv: S1..S6,
 // sw: W1..W6, the order of the formulas in include/pw.h), a u cell is read by
 // 16 (P, term) pairs, a v cell by 16, a w cell by 16; they are listed at the
-// three gather blocks below. Cotangents outside the computed points (halo
+// gather blocks below. Cotangents outside the computed points (halo
 // columns and rows, level 1, and level nz for sw) count as zero, so output
 // cells include the halo: gu, gv, gw are defined on every cell the forward
-// map reads. Each thread owns one cell column and marches k with a TMA ring
-// of the six fields (u, v, w, gsu, gsv, gsw) -- no atomics, one write per cell.
-// A launch splits the columns into k-chunks (blockIdx.z) so that small
-// domains still fill the GPU; a chunk of output levels kb..ke-1 reads levels
-// kb-1..ke.
+// map reads. Threads own cells (the paired kernel two, the FP32 kernel a
+// strip of four) and march k with a TMA ring of the six fields (u, v, w,
+// gsu, gsv, gsw) -- no atomics, one write per cell. A launch splits the
+// columns into k-chunks (blockIdx.z) so that small domains still fill the
+// GPU; a chunk of output levels kb..ke-1 reads levels kb-1..ke.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -49,36 +51,6 @@ struct AdjMaps {
     CUtensorMap m[kFields];  // u, v, w, gsu, gsv, gsw
 };
 
-template <typename T>
-struct AdjRing {
-    using Sh = AdjShape<T>;
-    unsigned char* base;
-    uint64_t* full;
-    __device__ __forceinline__ void setup(unsigned char* raw) {
-        base = raw + ((128u - (smem_addr(raw) & 127u)) & 127u);
-        full = reinterpret_cast<uint64_t*>(base + kS * Sh::STAGE_BYTES);
-    }
-    __device__ __forceinline__ const T* box(int slot, int f) const {
-        return reinterpret_cast<const T*>(base + slot * Sh::STAGE_BYTES + f * Sh::BOX_STRIDE);
-    }
-    // wait for load number `seq` (stage seq % kS, phase seq / kS)
-    __device__ __forceinline__ bool wait(int seq) {
-        return mbar_wait_bounded(&full[seq % kS], (uint32_t)((seq / kS) & 1));
-    }
-};
-
-// Load number `seq` of a chunk brings level `lev` (may be -1 or nz: the TMA
-// zero-fills out-of-range levels) into stage seq % kS.
-template <typename T>
-__device__ __forceinline__ void adj_issue(AdjRing<T>& r, const AdjMaps& maps, int seq, int lev, int x, int y) {
-    using Sh = AdjShape<T>;
-    const int s = seq % kS;
-    uint64_t* bar = &r.full[s];
-    unsigned char* dst = r.base + s * Sh::STAGE_BYTES;
-    mbar_arrive_expect_tx(bar, kFields * Sh::BOX_BYTES);
-    for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * Sh::BOX_STRIDE, &maps.m[f], bar, x, y, lev);
-}
-
 // The seven vertical coefficients step k uses (zero where the paper's level
 // has no such flux), in T. One thread each loads and converts them once per
 // level; the CTA barrier of the step before publishes them. (A per-thread
@@ -100,198 +72,6 @@ __device__ __forceinline__ double level_coef(const AdjArgs& a, int k, int n) {
 template <typename T>
 __device__ __forceinline__ void level_coefs(const AdjArgs& a, int k, int tid, T* dst) {
     if (tid < 7) dst[tid] = (T)level_coef(a, k, tid);
-}
-
-// Zero, in the staged cotangent boxes (gsu, gsv, gsw) of stage `slot`
-// (level lev), every cell that is not a computed output point of the forward
-// map: cells outside i = 1..nx, j = 1..ny, and whole boxes of levels where
-// the field is not computed (su, sv: levels 1..nz-1; sw: 1..nz-2). The
-// gather then needs no masks, and garbage (NaN included) in unused halo
-// cotangents never reaches a result. Only tiles at the domain edge and the
-// bottom and top levels have such cells. The writing threads order their
-// writes before the stage's next TMA load (fence.proxy.async).
-template <typename T>
-__device__ __forceinline__ void zero_outside(const AdjRing<T>& ring, int slot, int lev, const AdjArgs& a, int x0,
-                                             int y0, int tid) {
-    using Sh = AdjShape<T>;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const bool lev_s = lev >= 1 && lev <= nz - 1;
-    const bool lev_w = lev >= 1 && lev <= nz - 2;
-    // box column b holds cell i = i0 + b, box row r holds j = j0 + r
-    const int i0 = x0 - Sh::UNIT - a.xoff, j0 = y0 - 1;
-    const bool edge = i0 < 1 || i0 + Sh::BX - 1 > nx || j0 < 1 || j0 + Sh::BY - 1 > ny;
-    if (!edge && lev_s && lev_w) return;  // CTA-uniform
-    bool wrote = false;
-    for (int f = 3; f < kFields; ++f) {
-        const bool lv = (f == 5) ? lev_w : lev_s;
-        if (lv && !edge) continue;
-        T* box = const_cast<T*>(ring.box(slot, f));
-        for (int n = tid; n < Sh::BX * Sh::BY; n += kTX * kTY) {
-            const int r = n / Sh::BX, b = n - r * Sh::BX;
-            const int i = i0 + b, j = j0 + r;
-            if (!lv || i < 1 || i > nx || j < 1 || j > ny) {
-                box[n] = T(0);
-                wrote = true;
-            }
-        }
-    }
-    if (wrote) fence_proxy_async_smem();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kTX* kTY) adjoint_kernel(const __grid_constant__ AdjMaps maps, const AdjArgs a) {
-    using Sh = AdjShape<T>;
-    constexpr int BX = Sh::BX;
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ T coef_s[2][8];  // level coefficients, two levels in flight
-    AdjRing<T> ring;
-    ring.setup(smem_raw);
-
-    const int tid = threadIdx.x;
-    const int tx = tid % kTX, ty = tid / kTX;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-    const int i = x0 + tx, j = y0 + ty;  // output cell, halo included (0..nx+1, 0..ny+1)
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const bool act = (i <= nx + 1) && (j <= ny + 1);
-    const int bxs = x0 - Sh::UNIT;  // box x start (tensor coordinate), aligned
-    const int bys = y0 - 1;
-    const int kb = (int)((long long)nz * blockIdx.z / gridDim.z);
-    const int ke = (int)((long long)nz * (blockIdx.z + 1) / gridDim.z);
-    const int nseq = ke - kb + 2;   // loads: levels kb-1 .. ke
-
-    if (tid == 0) {
-        for (int f = 0; f < kFields; ++f) prefetch_tensormap(&maps.m[f]);
-        for (int s = 0; s < kS; ++s) mbar_init(&ring.full[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    int issued = 0;
-    if (tid == 0)
-        for (; issued < kS && issued < nseq; ++issued) adj_issue(ring, maps, issued, kb - 1 + issued, bxs, bys);
-
-    // shared index of cell (i, j): tensor x = i + xoff, box starts at bxs
-    const int c0 = (ty + 1) * BX + (tx + Sh::UNIT + a.xoff);
-    const T tcx = (T)a.tcx, tcy = (T)a.tcy;
-    T* __restrict__ gu = static_cast<T*>(a.gu);
-    T* __restrict__ gv = static_cast<T*>(a.gv);
-    T* __restrict__ gw = static_cast<T*>(a.gw);
-    size_t g = (size_t)j * (size_t)a.sy + (size_t)i + (size_t)kb * (size_t)a.sz;
-
-    bool bad = false;
-    // levels kb-1, kb, kb+1: each staged level's cotangents are cleaned
-    // (zero_outside) one step before the step that first reads it
-    for (int s = 0; s < 3 && s < nseq; ++s) {
-        const bool ok = ring.wait(s);
-        bad |= !ok;
-        if (ok) zero_outside(ring, s % kS, kb - 1 + s, a, x0, y0, tid);
-    }
-    level_coefs<T>(a, kb, tid, coef_s[0]);
-    bool abort = __syncthreads_or(bad);
-
-    for (int k = kb; k < ke && !abort; ++k) {
-        const int r = k - kb;
-        // next level's coefficient, loaded now so that its latency is hidden by the step
-        const double c_next = (tid < 7 && k + 1 < ke) ? level_coef(a, k + 1, tid) : 0.0;
-        if (r + 3 < nseq) {  // level k+2 (load r+3), read from the next step on
-            const bool ok = ring.wait(r + 3);
-            bad |= !ok;
-            if (ok) zero_outside(ring, (r + 3) % kS, k + 2, a, x0, y0, tid);
-        }
-        // stages of levels k-1, k, k+1
-        const int sm = r % kS, s0 = (r + 1) % kS, sp = (r + 2) % kS;
-        const T* Um = ring.box(sm, 0);
-        const T* U0 = ring.box(s0, 0);
-        const T* Up = ring.box(sp, 0);
-        const T* Vm = ring.box(sm, 1);
-        const T* V0 = ring.box(s0, 1);
-        const T* Vp = ring.box(sp, 1);
-        const T* Wm = ring.box(sm, 2);
-        const T* W0 = ring.box(s0, 2);
-        const T* Wp = ring.box(sp, 2);
-        const T* GUm = ring.box(sm, 3);
-        const T* GU0 = ring.box(s0, 3);
-        const T* GUp = ring.box(sp, 3);
-        const T* GVm = ring.box(sm, 4);
-        const T* GV0 = ring.box(s0, 4);
-        const T* GVp = ring.box(sp, 4);
-        const T* GWm = ring.box(sm, 5);
-        const T* GW0 = ring.box(s0, 5);
-        const T* GWp = ring.box(sp, 5);
-        const T* cs = coef_s[r & 1];
-        const T tz1p = cs[0], tz2m = cs[1], tz20 = cs[2], td1p = cs[3], td10 = cs[4], td2m = cs[5], td20 = cs[6];
-        constexpr int E = 1, N = BX;
-
-        // cotangents (index: P = C + offset); cells that are not computed
-        // points were zeroed in the stages (zero_outside), and the upper
-        // flux of the top level is absent through its coefficient (tz20 = 0)
-        const T su_c = GU0[c0], su_e = GU0[c0 + E], su_w = GU0[c0 - E], su_n = GU0[c0 + N], su_s = GU0[c0 - N];
-        const T su_nw = GU0[c0 + N - E];
-        const T su_km = GUm[c0], su_kp = GUp[c0], su_kp_w = GUp[c0 - E];
-        const T sv_c = GV0[c0], sv_e = GV0[c0 + E], sv_w = GV0[c0 - E], sv_n = GV0[c0 + N], sv_s = GV0[c0 - N];
-        const T sv_se = GV0[c0 - N + E];
-        const T sv_km = GVm[c0], sv_kp = GVp[c0], sv_kp_s = GVp[c0 - N];
-        const T sw_c = GW0[c0], sw_e = GW0[c0 + E], sw_w = GW0[c0 - E], sw_n = GW0[c0 + N], sw_s = GW0[c0 - N];
-        const T sw_km = GWm[c0], sw_km_e = GWm[c0 + E], sw_km_n = GWm[c0 + N];
-        const T sw_kp = GWp[c0];
-
-        // fields around C
-        const T u_c = U0[c0], u_e = U0[c0 + E], u_w = U0[c0 - E], u_n = U0[c0 + N], u_nw = U0[c0 + N - E];
-        const T u_kp = Up[c0], u_kp_w = Up[c0 - E];
-        const T v_c = V0[c0], v_e = V0[c0 + E], v_n = V0[c0 + N], v_s = V0[c0 - N], v_se = V0[c0 - N + E];
-        const T v_kp = Vp[c0], v_kp_s = Vp[c0 - N];
-        const T w_c = W0[c0], w_e = W0[c0 + E], w_n = W0[c0 + N];
-        const T w_kmc = Wm[c0], w_kme = Wm[c0 + E], w_kmn = Wm[c0 + N];
-        const T w_kp = Wp[c0];
-
-        // gu(C): T1 (P=C+x, P=C), T2 (P=C-x, P=C), T3 (P=C+y), T4 (P=C-y),
-        // T5 (P=C+z), T6 (P=C-z), S3 (P=C+x, P=C+x-y), S4 (P=C, P=C-y),
-        // W1 (P=C+x, P=C+x-z), W2 (P=C, P=C-z)
-        T r_u = tcx * ((u_e + u_c + u_c) * su_e + u_w * su_c - (u_w + u_c + u_c) * su_w - u_e * su_c);
-        r_u += tcy * ((v_c + v_e) * su_n - (v_s + v_se) * su_s);
-        r_u += tz1p * (w_c + w_e) * su_kp - tz2m * (w_kmc + w_kme) * su_km;
-        r_u += tcx * (v_c * sv_e + v_s * sv_se - v_e * sv_c - v_se * sv_s);
-        r_u += tcx * (w_c * sw_e + w_kmc * sw_km_e - w_e * sw_c - w_kme * sw_km);
-        // gv(C): mirror of the first four lines; T3 (P=C+y, P=C+y-x), T4 (P=C, P=C-x);
-        // W3 (P=C+y, P=C+y-z), W4 (P=C, P=C-z)
-        T r_v = tcy * ((v_n + v_c + v_c) * sv_n + v_s * sv_c - (v_s + v_c + v_c) * sv_s - v_n * sv_c);
-        r_v += tcx * ((u_c + u_n) * sv_e - (u_w + u_nw) * sv_w);
-        r_v += tz1p * (w_c + w_n) * sv_kp - tz2m * (w_kmc + w_kmn) * sv_km;
-        r_v += tcy * (u_c * su_n + u_w * su_nw - u_n * su_c - u_nw * su_w);
-        r_v += tcy * (w_c * sw_n + w_kmc * sw_km_n - w_n * sw_c - w_kmn * sw_km);
-        // gw(C): T5 (P=C+z, P=C+z-x), T6 (P=C, P=C-x), S5 (P=C+z, P=C+z-y),
-        // S6 (P=C, P=C-y), W1 (P=C+x), W2 (P=C-x), W3 (P=C+y), W4 (P=C-y),
-        // W5 (P=C+z, P=C), W6 (P=C-z, P=C)
-        T r_w = tz1p * (u_c * su_kp + u_w * su_kp_w) - tz20 * (u_kp * su_c + u_kp_w * su_w);
-        r_w += tz1p * (v_c * sv_kp + v_s * sv_kp_s) - tz20 * (v_kp * sv_c + v_kp_s * sv_s);
-        r_w += tcx * ((u_c + u_kp) * sw_e - (u_w + u_kp_w) * sw_w);
-        r_w += tcy * ((v_c + v_kp) * sw_n - (v_s + v_kp_s) * sw_s);
-        r_w += td1p * (w_kp + w_c + w_c) * sw_kp + td10 * w_kmc * sw_c;
-        r_w -= td2m * (w_kmc + w_c + w_c) * sw_km + td20 * w_kp * sw_c;
-
-        if (act) {
-            if (a.accumulate) {
-                gu[g] += r_u;
-                gv[g] += r_v;
-                gw[g] += r_w;
-            } else {
-                gu[g] = r_u;
-                gv[g] = r_v;
-                gw[g] = r_w;
-            }
-        }
-        g += (size_t)a.sz;
-        if (tid < 7 && k + 1 < ke) coef_s[(r + 1) & 1][tid] = (T)c_next;
-        abort = __syncthreads_or(bad);  // level k-1's stage is free
-        if (!abort && tid == 0 && issued < nseq) {
-            fence_proxy_async_smem();
-            adj_issue(ring, maps, issued, kb - 1 + issued, bxs, bys);
-            ++issued;
-        }
-    }
-    if (abort && tid == 0) {
-        atomicOr(&tu_status, kStatusTimeout);
-        for (int s = (issued > kS ? issued - kS : 0); s < issued; ++s) (void)ring.wait(s);
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -643,7 +423,7 @@ __global__ void fold_halo_x_kernel(T* f, int nx, int ny, int nz, long long sy, l
 }
 
 // ---------------------------------------------------------------------------
-// FP32 adjoint on strips (PW_F32): the gather of adjoint_kernel, with each
+// FP32 adjoint on strips (PW_F32): the cell-by-cell gather, with each
 // thread owning four consecutive cells along x. Tiles are laid out in the
 // TMA tensor's x coordinate X = i + xoff (the descriptor starts at the
 // 16-byte boundary at or below i = 0), so a strip's first cell sits at a
@@ -678,7 +458,7 @@ struct StripShape {
 };
 
 // Zero the cotangent cells of a staged level that are not computed output
-// points (as zero_outside, for the strip box geometry).
+// points (the paired kernel does the same while it splits a level).
 __device__ __forceinline__ void zero_outside_strip(unsigned char* stage, int lev, const AdjArgs& a, int X0, int y0,
                                                    int tid) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -923,32 +703,19 @@ TileShape adjoint_shape(int elem_bytes) {
     return TileShape{kSTX, kSTY, StripShape::BX, StripShape::BY, StripShape::SMEM_BYTES, kSNT};
 }
 
-cudaError_t launch_adjoint(const CUtensorMap* maps6, int elem_bytes, const AdjArgs& a, cudaStream_t st) {
+cudaError_t launch_adjoint(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st) {
     AdjMaps m;
     for (int f = 0; f < kFields; ++f) m.m[f] = maps6[f];
-    const int tx = (a.nx + 2 + kTX - 1) / kTX, ty = (a.ny + 2 + kTY - 1) / kTY;
-    const long long tiles = (long long)tx * ty;
-    cudaError_t e;
+    // strips of four cells, tiles laid out in tensor x = i + xoff
+    const int sx = (a.nx + 2 + a.xoff + kSTX - 1) / kSTX, sy = (a.ny + 2 + kSTY - 1) / kSTY;
+    cudaError_t e = cudaFuncSetAttribute(adjoint_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         StripShape::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     int chunks = 1;
-    if (elem_bytes == 8) {
-        e = cudaFuncSetAttribute(adjoint_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 AdjShape<double>::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        if ((e = choose_kchunks(adjoint_kernel<double>, kTX * kTY, AdjShape<double>::SMEM_BYTES, tiles, a.nz,
-                                &chunks)) != cudaSuccess)
-            return e;
-        adjoint_kernel<double><<<dim3(tx, ty, chunks), kTX * kTY, AdjShape<double>::SMEM_BYTES, st>>>(m, a);
-    } else {
-        // strips of four cells, tiles laid out in tensor x = i + xoff
-        const int sx = (a.nx + 2 + a.xoff + kSTX - 1) / kSTX, sy = (a.ny + 2 + kSTY - 1) / kSTY;
-        e = cudaFuncSetAttribute(adjoint_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 StripShape::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        if ((e = choose_kchunks(adjoint_strip_kernel, kSNT, StripShape::SMEM_BYTES, (long long)sx * sy, a.nz,
-                                &chunks)) != cudaSuccess)
-            return e;
-        adjoint_strip_kernel<<<dim3(sx, sy, chunks), kSNT, StripShape::SMEM_BYTES, st>>>(m, a);
-    }
+    if ((e = choose_kchunks(adjoint_strip_kernel, kSNT, StripShape::SMEM_BYTES, (long long)sx * sy, a.nz,
+                            &chunks)) != cudaSuccess)
+        return e;
+    adjoint_strip_kernel<<<dim3(sx, sy, chunks), kSNT, StripShape::SMEM_BYTES, st>>>(m, a);
     return cudaGetLastError();
 }
 

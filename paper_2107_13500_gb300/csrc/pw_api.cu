@@ -451,7 +451,7 @@ extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, c
             if (overlap(ptrs[o], ext, ptrs[n], ext))
                 return fail(PW_EALIAS, "%s: output %s overlaps %s", who, names[o], names[n]);
     }
-    const pw::TileShape shp = pw::adjoint_shape(es);
+    const pw::TileShape shp = dtype == PW_F64 ? pw::adjoint_f64_shape() : pw::adjoint_shape(es);
     CUtensorMap maps[6];
     for (int n = 0; n < 6; ++n)
         if ((rc = make_field_map(&maps[n], ptrs[n], es, *dims, shp.box_x, shp.box_y))) return rc;
@@ -468,6 +468,12 @@ extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, c
     a.tzc2 = c->tzc2;
     a.tzd1 = c->tzd1;
     a.tzd2 = c->tzd2;
+    a.u = u;
+    a.v = v;
+    a.w = w;
+    a.gsu = gsu;
+    a.gsv = gsv;
+    a.gsw = gsw;
     a.gu = gu;
     a.gv = gv;
     a.gw = gw;
@@ -476,8 +482,10 @@ extern "C" int pw_advect_adjoint(pw_dtype dtype, const void* u, const void* v, c
              (uintptr_t)gw % 16 == (uintptr_t)u % 16)
                 ? 1
                 : 0;
-    cudaError_t e = dtype == PW_F64_PAIRED ? pw::launch_adjoint_paired(maps, a, static_cast<cudaStream_t>(stream))
-                                           : pw::launch_adjoint(maps, es, a, static_cast<cudaStream_t>(stream));
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = dtype == PW_F64          ? pw::launch_adjoint_f64(maps, a, st)
+                    : dtype == PW_F64_PAIRED ? pw::launch_adjoint_paired(maps, a, st)
+                                             : pw::launch_adjoint(maps, a, st);
     if (e != cudaSuccess) return cuda_fail(e, who);
     return PW_OK;
 }

@@ -278,14 +278,20 @@ struct AdjArgs {
     int xoff;                  // elements from the descriptors' 16-byte base to i = 0
     double tcx, tcy;
     const double *tzc1, *tzc2, *tzd1, *tzd2;
+    const void *u, *v, *w;        // the fields and cotangents, for kernels that read them
+    const void *gsu, *gsv, *gsw;  // with plain loads (the FP64 halo cells)
     void *gu, *gv, *gw;
     int accumulate;
     int vec;                   // gu, gv, gw have u's address modulo 16 bytes (16-byte stores of strips)
 };
 
+// PW_F32 (elem_bytes 4, strips) and PW_F64_PAIRED (elem_bytes 8)
 TileShape adjoint_shape(int elem_bytes);
-// maps6: u, v, w, gsu, gsv, gsw
-cudaError_t launch_adjoint(const CUtensorMap* maps6, int elem_bytes, const AdjArgs& a, cudaStream_t st);
+// maps6: u, v, w, gsu, gsv, gsw; PW_F32
+cudaError_t launch_adjoint(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st);
+// PW_F64: the face-form kernel and its halo-cell kernel
+TileShape adjoint_f64_shape();
+cudaError_t launch_adjoint_f64(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st);
 // PW_F64_PAIRED: double fields, the box of adjoint_shape(8)
 cudaError_t launch_adjoint_paired(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st);
 cudaError_t launch_fold_halo(void* field, int elem_bytes, int nx, int ny, int nz, long long sy, long long sz,
@@ -310,5 +316,6 @@ cudaError_t read_and_clear_status_paired(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_split(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_adjoint(unsigned int* status, cudaStream_t st);
 cudaError_t read_and_clear_status_f64(unsigned int* status, cudaStream_t st);
+cudaError_t read_and_clear_status_adjoint_f64(unsigned int* status, cudaStream_t st);
 
 }  // namespace pw

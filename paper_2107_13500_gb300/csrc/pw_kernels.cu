@@ -368,13 +368,14 @@ cudaError_t launch_selftest_wait(unsigned long long limit_ns, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 
 cudaError_t read_and_clear_status(unsigned int* status, cudaStream_t st) {
-    unsigned int parts[5] = {0, 0, 0, 0, 0};
+    unsigned int parts[6] = {0, 0, 0, 0, 0, 0};
     cudaError_t e = read_and_clear_tu_status(&parts[0], st);
     if (e == cudaSuccess) e = read_and_clear_status_paired(&parts[1], st);
     if (e == cudaSuccess) e = read_and_clear_status_split(&parts[2], st);
     if (e == cudaSuccess) e = read_and_clear_status_adjoint(&parts[3], st);
     if (e == cudaSuccess) e = read_and_clear_status_f64(&parts[4], st);
-    *status = parts[0] | parts[1] | parts[2] | parts[3] | parts[4];
+    if (e == cudaSuccess) e = read_and_clear_status_adjoint_f64(&parts[5], st);
+    *status = parts[0] | parts[1] | parts[2] | parts[3] | parts[4] | parts[5];
     return e;
 }
 

@@ -31,7 +31,8 @@ def _raw(nx, ny, nz, seed, stream, lo=-1.0, hi=1.0):
 
 
 @pytest.mark.parametrize("mode,dtype_name", [("f64", "float64"), ("paired", "float64"), ("f32", "float32")])
-@pytest.mark.parametrize("shape", [(37, 13, 6), (64, 8, 3), (5, 3, 2), (33, 9, 1), (70, 20, 40)])
+@pytest.mark.parametrize("shape", [(37, 13, 6), (64, 8, 3), (5, 3, 2), (33, 9, 1), (70, 20, 40), (1, 1, 3),
+                                   (96, 24, 9)])
 @pytest.mark.parametrize("aligned", [True, False])
 def test_adjoint_matches_oracle(gpu, oracle_lib, mode, dtype_name, shape, aligned):
     """Gather-form GPU adjoint vs the oracle's scatter form, every cell the
