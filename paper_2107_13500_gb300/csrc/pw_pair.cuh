@@ -50,23 +50,25 @@ __device__ __forceinline__ pf pmul(pf a, pf b) {
     return {p, e};
 }
 
-// Split a double into (h, l): h = d truncated to 24 significant bits, l =
-// float(d - h) (the 29 dropped bits, rounded to 24: same sign as d, below
-// one unit of h's last place). |d - (h + l)| <= 2^-48 |d|. Valid for
+// Split a double into (h, l): h = d rounded to 24 significant bits (ties
+// away from zero), l = float(d - h). |d - (h + l)| <= 2^-49 |d|. Valid for
 // 2^-74 <= |d| < 2^128; zero and smaller magnitudes give (0, 0). The words
 // are read as 32-bit integers: tests written on the 64-bit pattern can be
 // turned into FP64 comparisons by the compiler.
 __device__ __forceinline__ pf split_double(double d) {
     const unsigned hw = static_cast<unsigned>(__double2hiint(d));
     const unsigned lw = static_cast<unsigned>(__double2loint(d));
-    // the high-word term moves the exponent bias from 1023 to 127 (896 << 20)
-    const unsigned t = hw + 0xC8000000u;
-    const unsigned hb = __funnelshift_l(lw, t, 3) | (hw & 0x80000000u);
+    // the high-word term moves the exponent bias from 1023 to 127 (896 << 20);
+    // h rounds up when the 29 dropped bits are at least half its last unit
+    const unsigned up = (lw >> 28) & 1u;
+    const unsigned hb = (__funnelshift_l(lw, hw + 0xC8000000u, 3) + up) | (hw & 0x80000000u);
+    // the dropped bits as a signed count of d's last-bit unit (minus 2^29 when h rounded up)
+    const int rem = static_cast<int>(lw << 3) >> 3;
     const unsigned ex = hw & 0x7FF00000u;
     // +-2^(E - 1075) (E = d's biased exponent): the weight of d's last bit
     const unsigned sb = ((ex - (948u << 20)) << 3) | (hw & 0x80000000u);
     const float hi = __uint_as_float(hb);
-    const float lo = __int2float_rn(static_cast<int>(lw & 0x1FFFFFFFu)) * __uint_as_float(sb);
+    const float lo = __int2float_rn(rem) * __uint_as_float(sb);
     const bool tiny = ex < (949u << 20);
     return {tiny ? 0.0f : hi, tiny ? 0.0f : lo};
 }
