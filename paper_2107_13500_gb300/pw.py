@@ -304,19 +304,39 @@ def advect(u, v, w, coeffs: Coefficients, nx, ny, mode="paired", split_table=Non
 
 
 class HostPipeline:
-    """Device staging buffers and three streams for advect_host: reuse one
-    across calls on same-shaped fields. It remembers when the previous call's
-    kernels finished (its device inputs are free) and when its outputs left
-    the device (its device outputs are free), so that the next call's input
-    copies overlap the previous call's output copies."""
+    """Device staging buffers and three streams (host->device, compute,
+    device->host) for advect_host: reuse one across calls on same-shaped
+    fields. It holds `depth` sets of the six staging fields and uses them in
+    turn, so that consecutive calls overlap: a call's input copies wait only
+    until the kernels of the call that last used its set have finished, and
+    its kernels only until that call's outputs have left the device. With two
+    sets, one call's outputs stream out while the next call's inputs stream in
+    and its slabs compute."""
 
-    def __init__(self, nx, ny, nz, dtype=None, device="cuda"):
+    def __init__(self, nx, ny, nz, dtype=None, device="cuda", depth=2):
         import torch
         dtype = dtype or torch.float64
-        self.dev = [empty_field(nx, ny, nz, dtype, device) for _ in range(6)]
+        if depth < 1:
+            raise ValueError("depth must be >= 1")
+        self.sets = [[empty_field(nx, ny, nz, dtype, device) for _ in range(6)] for _ in range(depth)]
+        self.dev = self.sets[0]
         self.streams = [torch.cuda.Stream(device=device) for _ in range(3)]
-        self.compute_done = None
-        self.d2h_done = None
+        self.compute_done = [None] * depth  # per set: the last call's kernels done (its inputs are free)
+        self.d2h_done = [None] * depth      # per set: the last call's outputs copied out (its outputs are free)
+        self.done = None                     # the latest call's outputs are in host memory
+        self.calls = 0
+
+    def wait(self, stream=None):
+        """Order `stream` (default: the current stream) after the latest
+        call's outputs reaching host memory."""
+        import torch
+        if self.done is not None:
+            (stream or torch.cuda.current_stream()).wait_event(self.done)
+
+    def synchronize(self):
+        """Block the host until the latest call's outputs are in host memory."""
+        if self.done is not None:
+            self.done.synchronize()
 
 
 def pinned_field(nx, ny, nz, dtype=None):
@@ -330,50 +350,61 @@ def pinned_field(nx, ny, nz, dtype=None):
 def advect_host(u_h, v_h, w_h, coeffs: Coefficients, nx, ny, mode="paired", out_host=None, pipeline=None,
                 nchunks=8, split_table=None, wait=True):
     """pw_advect on pinned host fields with chunked, overlapped transfers
-    (pw_advect_host_chunked). Returns the host outputs; with wait=True the
-    call returns after they have arrived, otherwise the caller's current
-    stream is ordered after their arrival. The host inputs are read when the
-    input copies run, which may be before earlier work on the caller's
-    stream: they must be complete in host memory when the call is made."""
+    (pw_advect_host_chunked). Returns the host outputs. The call's kernels
+    are ordered after the caller's current stream (coefficients, tables).
+    With wait=True it returns once the outputs have arrived. With
+    wait=False it returns after enqueueing: on a caller's `pipeline`, the
+    outputs are in host memory once pipeline.done has completed
+    (pipeline.wait(stream), pipeline.synchronize()), and later calls on the
+    pipeline overlap this one; without one, the caller's current stream is
+    ordered after their arrival. The host inputs are read when the input
+    copies run, which may be before earlier work on the caller's stream: they
+    must be complete in host memory when the call is made."""
     import torch
     lib = load_library()
     dt = MODES[mode]
     nz = u_h.shape[0]
     d = dims_of(u_h, nx, ny)
-    if pipeline is None:
-        pipeline = HostPipeline(nx, ny, nz, u_h.dtype)
+    own = pipeline is None
+    if own:
+        pipeline = HostPipeline(nx, ny, nz, u_h.dtype, depth=1)
     if out_host is None:
         out_host = tuple(torch.zeros_like(u_h).pin_memory() for _ in range(3))
     if mode == "f32" and split_table is None:
         split_table = coeffs.zero_mean_table()
-    for t in pipeline.dev:
+    k = pipeline.calls % len(pipeline.sets)
+    dev = pipeline.sets[k]
+    for t in dev:
         if t.stride() != u_h.stride():
             raise ValueError("host and device fields must share strides")
     c = coeffs.c_struct()
     vp = ctypes.c_void_p
     sh, sc, sd = pipeline.streams
     cur = torch.cuda.current_stream()
-    # input copies: only the staging inputs must be free (previous kernels done)
-    if pipeline.compute_done is not None:
-        sh.wait_event(pipeline.compute_done)
-    # kernels: the caller's device work (coefficients, tables) and the
-    # previous call's outputs drained from the staging outputs
+    # input copies: this set's staging inputs must be free (its last kernels done)
+    if pipeline.compute_done[k] is not None:
+        sh.wait_event(pipeline.compute_done[k])
+    # kernels: the caller's device work (coefficients, tables), and this
+    # set's staging outputs drained by its last call
     sc.wait_stream(cur)
-    if pipeline.d2h_done is not None:
-        sc.wait_event(pipeline.d2h_done)
+    if pipeline.d2h_done[k] is not None:
+        sc.wait_event(pipeline.d2h_done[k])
     sd.wait_stream(cur)
     _check(lib.pw_advect_host_chunked(dt, *(vp(t.data_ptr()) for t in (u_h, v_h, w_h) + tuple(out_host)),
-                                      *(vp(t.data_ptr()) for t in pipeline.dev), ctypes.byref(c), ctypes.byref(d),
+                                      *(vp(t.data_ptr()) for t in dev), ctypes.byref(c), ctypes.byref(d),
                                       None if split_table is None else vp(split_table.data_ptr()), int(nchunks),
                                       vp(sh.cuda_stream), vp(sc.cuda_stream), vp(sd.cuda_stream)))
-    pipeline.compute_done = torch.cuda.Event()
-    pipeline.compute_done.record(sc)
-    pipeline.d2h_done = torch.cuda.Event()
-    pipeline.d2h_done.record(sd)
+    pipeline.compute_done[k] = torch.cuda.Event()
+    pipeline.compute_done[k].record(sc)
+    pipeline.d2h_done[k] = torch.cuda.Event()
+    pipeline.d2h_done[k].record(sd)
     # the output copies follow every kernel and input copy of the call
-    cur.wait_event(pipeline.d2h_done)
+    pipeline.done = pipeline.d2h_done[k]
+    pipeline.calls += 1
     if wait:
         sd.synchronize()
+    elif own:
+        cur.wait_event(pipeline.done)
     return out_host
 
 
