@@ -78,7 +78,7 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 // levels are walked top down, the reverse of the mean pass, so the levels
 // that pass read last are read again while they are still in L2.
 
-constexpr int kSplitThreads = 256, kSplitCluster = 8, kSplitUnroll = 8;
+constexpr int kSplitThreads = 512, kSplitCluster = 8, kSplitUnroll = 16;
 constexpr int kPertThreads = 128, kPertRows = 8;  // columns per CTA, rows per thread
 
 // Biased double exponents of the magnitudes the paired sum carries: [2^-60, 2^100).
