@@ -61,8 +61,12 @@ SOURCE_DIRS = (os.path.join(ROOT, "paper_2107_13500_gb300", "csrc"), os.path.joi
 # FP64 lane operations per point of the native kernel's scheme on its 32 x 16
 # tile: scaling tcx u and tcy v over the cells the faces read ((17*34 + 18*33)
 # / 512), the six horizontal face-sum types ((3*16*33 + 3*17*32) / 512), three
-# vertical face sums, six vertical coefficient products, 18 face products.
-F64_OPS_PER_POINT = (17 * 34 + 18 * 33) / 512 + (3 * 16 * 33 + 3 * 17 * 32) / 512 + 3 + 6 + 18
+# vertical face sums, 18 face products, and the vertical coefficient products:
+# three (one per output, shared by the level's two vertical face terms) when
+# every level's two vertical coefficients are equal, as on the benchmark's
+# grid (no density stratification), else six.
+F64_OPS_PER_POINT_DENSITY = (17 * 34 + 18 * 33) / 512 + (3 * 16 * 33 + 3 * 17 * 32) / 512 + 3 + 18 + 6
+F64_OPS_PER_POINT = F64_OPS_PER_POINT_DENSITY - 3
 # FP64 pipe: GB300 retires 2 FP64 lane operations per clock per SM (an FMA
 # counted once): 152 SMs x 2 x 2.07 GHz (maximum SM clock).
 FP64_PIPE_PEAK_GOPS = 152 * 2 * 2.07e9 / 1e9
@@ -534,7 +538,8 @@ def main():
     bpp = pw.BYTES_PER_POINT[mode]
     achieved = bpp * pts / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": stored_traffic(mode), "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json)",
+                "traffic": stored_traffic(mode), "peak_kind": ("measured copy bandwidth (MEASURED_PEAKS.json)" if peak_kind == "measured" else
+                                         "fallback copy bandwidth (6.8 TB/s; MEASURED_PEAKS.json absent)"),
                 "algorithmic_bytes_per_launch": bpp * pts,
                 "kernel": f"{KERNEL_NAMES[mode]} (pw_advect[{mode}], one launch per step)"}
     if mode == "f64":

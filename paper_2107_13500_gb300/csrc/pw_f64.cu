@@ -19,11 +19,18 @@
 //   faces   the six horizontal face-sum types of the level, each face once,
 //           into shared arrays (a flat list of items over all threads);
 //   points  one thread per point: the three vertical face sums (carried to
-//           the next level in registers, scaled by that level's
-//           coefficient), then each output as one multiply and five FMAs.
+//           the next level in registers), then each output from its six
+//           face products.
+// A level's two vertical face terms carry the coefficients tzc1(k) and
+// tzc2(k) (tzd1, tzd2 for sw), which differ only with density
+// stratification. Where they are equal on every level (checked per domain on
+// the device, bit for bit), the two terms share one product:
+// c(k) (q(k-1) F(k-1/2) - q(k+1) F(k+1/2)); otherwise each face sum is
+// scaled by its own coefficient.
 // FP64 operations per point (32 x 16 tile): about 2.3 scaling, 6.3 face
-// sums, 3 vertical sums, 6 vertical coefficient products, 18 face products:
-// about 36, against about 48 for the term-by-term evaluation.
+// sums, 3 vertical sums, 18 face products, and 3 vertical coefficient
+// products (6 with density): about 32.6 (35.6), against about 48 for the
+// term-by-term evaluation.
 //
 // Levels arrive through the TMA ring of pw_ring.cuh (u, v, w boxes of the
 // tile plus its one-cell halo). Step k reads boxes k and k+1 and scales
@@ -139,6 +146,22 @@ struct F64K {
         }
     }
 
+    // True when every level's two vertical coefficients are the same number:
+    // tzc1(k) = tzc2(k) wherever su and sv have an upper flux, tzd1(k) =
+    // tzd2(k) wherever sw is computed (a grid without density stratification).
+    // The answer depends on the domain only, so every tile of it, one-shot or
+    // batched, takes the same arithmetic. Compared as 32-bit words: a
+    // comparison of doubles issues on the FP64 pipe.
+    static __device__ bool vertical_pairs_equal(const FwdArgs& a, int tid) {
+        auto same = [](double x, double y) {
+            return __double2hiint(x) == __double2hiint(y) && __double2loint(x) == __double2loint(y);
+        };
+        bool eq = true;
+        for (int k = 1 + tid; k <= a.nz - 2; k += C::NT)
+            eq &= same(__ldg(a.tzc1 + k), __ldg(a.tzc2 + k)) && same(__ldg(a.tzd1 + k), __ldg(a.tzd2 + k));
+        return __syncthreads_and(eq) != 0;
+    }
+
     // One tile (bx, by) of domain `a`, output levels kb..ke-1 (a chunk of the
     // column; it reads one level below and one above). `seq` is the CTA's
     // running load count; loads are numbered relative to the lowest level
@@ -147,6 +170,19 @@ struct F64K {
     static __device__ bool tile(Ring<Shape>& ring, const Smem& sm, const CUtensorMap* mu, const CUtensorMap* mv,
                                 const CUtensorMap* mw, const FwdArgs& a, int bx, int by, int kb, int ke, long long& seq,
                                 int tid) {
+        if (vertical_pairs_equal(a, tid))
+            return tile_impl<true>(ring, sm, mu, mv, mw, a, bx, by, kb, ke, seq, tid);
+        return tile_impl<false>(ring, sm, mu, mv, mw, a, bx, by, kb, ke, seq, tid);
+    }
+
+    // kEq: the level's vertical face terms share one coefficient product,
+    // c(k) (q(k-1) F(k-1/2) - q(k+1) F(k+1/2)) with c = tzc1 = tzc2 (tzd1 =
+    // tzd2 for sw): one FP64 operation less per output than scaling each face
+    // sum by its own coefficient.
+    template <bool kEq>
+    static __device__ bool tile_impl(Ring<Shape>& ring, const Smem& sm, const CUtensorMap* mu, const CUtensorMap* mv,
+                                     const CUtensorMap* mw, const FwdArgs& a, int bx, int by, int kb, int ke,
+                                     long long& seq, int tid) {
         constexpr int S = C::S, BX = C::BX, TX = C::TX;
         const int tx = tid % TX, ty = tid / TX;
         const int x0 = bx * TX, y0 = by * C::TY;
@@ -181,8 +217,8 @@ struct F64K {
         const int k1 = kb > 1 ? kb : 1;                  // first computed level (lo = k1 - 1)
         bool bad = false, abort = false;
         // level-(k-1) values carried up the column: the point's own u, v, w,
-        // and its three vertical face sums scaled by level k's lower
-        // coefficients (tzc1(k) for su and sv, tzd1(k) for sw)
+        // and its three vertical face sums, scaled by level k's lower
+        // coefficients (tzc1(k) for su and sv, tzd1(k) for sw) unless kEq
         double uo = 0.0, vo = 0.0, wo = 0.0, w1x = 0.0, w1y = 0.0, c1 = 0.0;
 
         if (k1 < ke) {
@@ -196,10 +232,15 @@ struct F64K {
                 uo = ring.template box<double>(s0, 0)[c0];
                 vo = ring.template box<double>(s0, 1)[c0];
                 wo = W0[c0];
-                const double t1 = __ldg(a.tzc1 + k1), d1 = __ldg(a.tzd1 + k1);
-                w1x = __dmul_rn(t1, __dadd_rn(wo, W0[c0 + 1]));
-                w1y = __dmul_rn(t1, __dadd_rn(wo, W0[c0 + BX]));
-                c1 = __dmul_rn(d1, __dadd_rn(wo, W1[c0]));
+                w1x = __dadd_rn(wo, W0[c0 + 1]);
+                w1y = __dadd_rn(wo, W0[c0 + BX]);
+                c1 = __dadd_rn(wo, W1[c0]);
+                if (!kEq) {
+                    const double t1 = __ldg(a.tzc1 + k1), d1 = __ldg(a.tzd1 + k1);
+                    w1x = __dmul_rn(t1, w1x);
+                    w1y = __dmul_rn(t1, w1y);
+                    c1 = __dmul_rn(d1, c1);
+                }
             }
             scale_level(ring, sm, s0 + 1, k1, xoff, tcx, tcy, tid);
             if (!top1) scale_level(ring, sm, s0 + 2, k1 + 1, xoff, tcx, tcy, tid);
@@ -234,34 +275,56 @@ struct F64K {
             ru = __fma_rn(-U[c0 + 1], fx0[fxw + 1], ru);
             ru = __fma_rn(U[c0 - BX], fy0[fys], ru);
             ru = __fma_rn(-U[c0 + BX], fy0[fys + C::FYW], ru);
-            ru = __fma_rn(uo, w1x, ru);
             // sv: y first (its own direction), then x, then z
             double rv = __dmul_rn(V[c0 - BX], fy1[fys]);
             rv = __fma_rn(-V[c0 + BX], fy1[fys + C::FYW], rv);
             rv = __fma_rn(V[c0 - 1], fx1[fxw], rv);
             rv = __fma_rn(-V[c0 + 1], fx1[fxw + 1], rv);
-            rv = __fma_rn(vo, w1y, rv);
+            // the lower vertical terms (their coefficient is applied below if kEq)
+            double zu = 0.0, zv = 0.0;
+            if (kEq) {
+                zu = __dmul_rn(uo, w1x);
+                zv = __dmul_rn(vo, w1y);
+            } else {
+                ru = __fma_rn(uo, w1x, ru);
+                rv = __fma_rn(vo, w1y, rv);
+            }
             double rw = 0.0;
             if (!top) {
                 const double* U1 = ring.template box<double>(s0 + r + 1, 0);
                 const double* V1 = ring.template box<double>(s0 + r + 1, 1);
                 const double* W1 = ring.template box<double>(s0 + r + 1, 2);
-                const double tz2 = __ldg(a.tzc2 + k), td2 = __ldg(a.tzd2 + k);
-                const double tn1 = __ldg(a.tzc1 + k + 1), dn1 = __ldg(a.tzd1 + k + 1);
                 const double wu = W1[c0];
                 const double ck = __dadd_rn(wc, wu);  // w face sum of sw's upper face
-                ru = __fma_rn(-U1[c0], __dmul_rn(tz2, wxk), ru);
-                rv = __fma_rn(-V1[c0], __dmul_rn(tz2, wyk), rv);
                 // sw: x (w advected by tcx (u(k) + u(k+1))), y, z (by w)
                 rw = __dmul_rn(W[c0 - 1], fx2[fxw]);
                 rw = __fma_rn(-W[c0 + 1], fx2[fxw + 1], rw);
                 rw = __fma_rn(W[c0 - BX], fy2[fys], rw);
                 rw = __fma_rn(-W[c0 + BX], fy2[fys + C::FYW], rw);
-                rw = __fma_rn(wo, c1, rw);
-                rw = __fma_rn(-wu, __dmul_rn(td2, ck), rw);
-                w1x = __dmul_rn(tn1, wxk);
-                w1y = __dmul_rn(tn1, wyk);
-                c1 = __dmul_rn(dn1, ck);
+                if (kEq) {
+                    zu = __fma_rn(-U1[c0], wxk, zu);
+                    zv = __fma_rn(-V1[c0], wyk, zv);
+                    const double zw = __fma_rn(-wu, ck, __dmul_rn(wo, c1));
+                    rw = __fma_rn(__ldg(a.tzd1 + k), zw, rw);
+                    w1x = wxk;
+                    w1y = wyk;
+                    c1 = ck;
+                } else {
+                    const double tz2 = __ldg(a.tzc2 + k), td2 = __ldg(a.tzd2 + k);
+                    const double tn1 = __ldg(a.tzc1 + k + 1), dn1 = __ldg(a.tzd1 + k + 1);
+                    ru = __fma_rn(-U1[c0], __dmul_rn(tz2, wxk), ru);
+                    rv = __fma_rn(-V1[c0], __dmul_rn(tz2, wyk), rv);
+                    rw = __fma_rn(wo, c1, rw);
+                    rw = __fma_rn(-wu, __dmul_rn(td2, ck), rw);
+                    w1x = __dmul_rn(tn1, wxk);
+                    w1y = __dmul_rn(tn1, wyk);
+                    c1 = __dmul_rn(dn1, ck);
+                }
+            }
+            if (kEq) {
+                const double ck1 = __ldg(a.tzc1 + k);
+                ru = __fma_rn(ck1, zu, ru);
+                rv = __fma_rn(ck1, zv, rv);
             }
             if (act) {
                 su[g] = ru;
