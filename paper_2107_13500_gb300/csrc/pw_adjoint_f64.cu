@@ -148,8 +148,33 @@ struct Smem {
     }
 };
 
+// Offsets of b3 and b6 in a level's scale slot: with equal coefficients
+// they are a3 and a6. (At the top level, where b is 0 and a is not, every use
+// of b multiplies a value of the level above the domain, which reads as 0.)
+template <bool kEq>
+__device__ __forceinline__ constexpr int b3_off() { return kEq ? 0 : AF::NXP; }
+template <bool kEq>
+__device__ __forceinline__ constexpr int b6_off() { return kEq ? 2 * AF::NXP : 2 * AF::NXP + AF::NYP; }
+
+// True when every level's two vertical coefficients are the same number
+// (tzc1(k) = tzc2(k) and tzd1(k) = tzd2(k) on levels 1..nz-2: a grid without
+// density stratification); the same answer for every tile of a domain.
+// Compared as 32-bit words (a comparison of doubles issues on the FP64 pipe).
+__device__ __forceinline__ bool vertical_pairs_equal(const AdjArgs& a, int tid) {
+    auto same = [](double x, double y) {
+        return __double2hiint(x) == __double2hiint(y) && __double2loint(x) == __double2loint(y);
+    };
+    bool eq = true;
+    for (int k = 1 + tid; k <= a.nz - 2; k += kNT)
+        eq &= same(__ldg(a.tzc1 + k), __ldg(a.tzc2 + k)) && same(__ldg(a.tzd1 + k), __ldg(a.tzd2 + k));
+    return __syncthreads_and(eq) != 0;
+}
+
 // a3 = tzc1 gsu, b3 = tzc2 gsu at the x positions, a6, b6 of gsv at the y
-// positions, of level lev (load seq) into slot lev & 1.
+// positions, of level lev (load seq) into slot lev & 1. kEq: the level's two
+// coefficients are equal, so only a3 and a6 are formed and stand for b3 and
+// b6 too (see b_off).
+template <bool kEq>
 __device__ __forceinline__ void scale_level(const Smem& sm, int seq, int lev, const AdjArgs& a, int tid) {
     const double* LU = sm.box(seq, 3) + a.xoff;
     const double* LV = sm.box(seq, 4) + a.xoff;
@@ -162,18 +187,19 @@ __device__ __forceinline__ void scale_level(const Smem& sm, int seq, int lev, co
             const int r = n / AF::XW, c = n - r * AF::XW;
             const double lu = LU[(r + 1) * AF::BX + c];
             s[n] = __dmul_rn(c1, lu);
-            s[AF::NXP + n] = __dmul_rn(c2, lu);
+            if (!kEq) s[AF::NXP + n] = __dmul_rn(c2, lu);
         } else if (n >= AF::YSLOT0 && n < AF::NSLOT) {
             const int m = n - AF::YSLOT0;
             const int r = m / AF::YW, c = m - r * AF::YW;
             const double lv = LV[r * AF::BX + c + 1];
             s[2 * AF::NXP + m] = __dmul_rn(c1, lv);
-            s[2 * AF::NXP + AF::NYP + m] = __dmul_rn(c2, lv);
+            if (!kEq) s[2 * AF::NXP + AF::NYP + m] = __dmul_rn(c2, lv);
         }
     }
 }
 
 // The shared items of level lev (load seq; the level above is load seq + 1).
+template <bool kEq>
 __device__ __forceinline__ void items_level(const Smem& sm, int seq, int lev, const AdjArgs& a, int tid) {
     const int xo = a.xoff;
     const double* U = sm.box(seq, 0) + xo;
@@ -197,7 +223,7 @@ __device__ __forceinline__ void items_level(const Smem& sm, int seq, int lev, co
             ix[kF4 * AF::NXP] = __dadd_rn(u0, un);
             ix[kF7 * AF::NXP] = __dadd_rn(u0, uk);
             ix[kP2 * AF::NXP] = __fma_rn(ln, u0, -__dmul_rn(l0, un));
-            ix[kP3 * AF::NXP] = __fma_rn(sa[n], u0, -__dmul_rn(sb[AF::NXP + n], uk));
+            ix[kP3 * AF::NXP] = __fma_rn(sa[n], u0, -__dmul_rn(sb[b3_off<kEq>() + n], uk));
         } else if (n >= AF::YSLOT0 && n < AF::NSLOT) {
             const int m = n - AF::YSLOT0;
             const int r = m / AF::YW, c = m - r * AF::YW;
@@ -209,27 +235,19 @@ __device__ __forceinline__ void items_level(const Smem& sm, int seq, int lev, co
             iy[kF2 * AF::NYP] = __dadd_rn(v0, ve);
             iy[kF8 * AF::NYP] = __dadd_rn(v0, vk);
             iy[kP4 * AF::NYP] = __fma_rn(le, v0, -__dmul_rn(l0, ve));
-            iy[kP6 * AF::NYP] = __fma_rn(sa[2 * AF::NXP + m], v0, -__dmul_rn(sb[2 * AF::NXP + AF::NYP + m], vk));
+            iy[kP6 * AF::NYP] = __fma_rn(sa[2 * AF::NXP + m], v0, -__dmul_rn(sb[b6_off<kEq>() + m], vk));
         }
     }
 }
 
-// One launch: CTAs [0, sched.items) each take one work item (a level chunk
-// of one tile, in the order of the one-shot schedule); the CTAs after them
-// gather the halo cells, one per thread, filling the schedule's last wave.
-__global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_constant__ AdjF64Maps maps, const AdjArgs a,
-                                                             const ItemSched sched) {
-    extern __shared__ unsigned char smem_raw[];
-    const int tid = threadIdx.x;
-    if ((long long)blockIdx.x >= sched.items) {  // CTA-uniform
-        adjoint_halo_cell<double>(a, ((long long)blockIdx.x - sched.items) * kNT + tid);
-        return;
-    }
-    Smem sm;
-    sm.setup(smem_raw);
-
-    int bx, by, kb, ke;
-    sched_item(sched, a.nz, blockIdx.x, &bx, &by, &kb, &ke);
+// One work item: output levels kb..ke-1 of the tile (bx, by). kEq: every
+// level's two vertical coefficients are equal; kSameT: tcx = tcy. Each lets
+// a product be shared (the b cotangents are the a ones; sw's per-level
+// scaled cotangent serves both its faces; x and y parts of an output take
+// one coefficient product).
+template <bool kEq, bool kSameT>
+__device__ __forceinline__ void adjoint_tile(const AdjF64Maps& maps, const AdjArgs& a, Smem& sm, int bx, int by,
+                                             int kb, int ke, int tid) {
     const int tx = tid % kTX, ty = tid / kTX;
     const int x0 = bx * kTX, y0 = by * kTY;
     const int i = x0 + 1 + tx, j = y0 + 1 + ty;  // interior cell
@@ -276,6 +294,7 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
     // cotangents of the level below
     double p7m = 0.0, p8m = 0.0, f3m = 0.0, f6m = 0.0, f9m = 0.0, p9m = 0.0;
     double b3m = 0.0, b6m = 0.0, b9m = 0.0, b3c = 0.0, b6c = 0.0;
+    double a9c = 0.0;  // kEq: tzd1(k) gsw(k), which is also sw's b cotangent of level k
     if (!abort) {
         const double* W = sm.box(0, 2);
         const double* LW = sm.box(0, 5);
@@ -293,8 +312,9 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
         b9m = __dmul_rn(coef_at(a.tzd2, kb - 1, nz), lc);
         const double a9 = __dmul_rn(coef_at(a.tzd1, kb, nz), sm.box(1, 5)[c0]);
         p9m = __fma_rn(a9, wc, -__dmul_rn(b9m, wk));
-        scale_level(sm, 1, kb, a, tid);
-        scale_level(sm, 2, kb + 1, a, tid);
+        a9c = a9;
+        scale_level<kEq>(sm, 1, kb, a, tid);
+        scale_level<kEq>(sm, 2, kb + 1, a, tid);
     }
     abort = __syncthreads_or(bad);  // load 0 is free
     if (!abort && tid == 0 && issued < nseq) {
@@ -303,10 +323,10 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
         ++issued;
     }
     if (!abort) {
-        items_level(sm, 1, kb, a, tid);
+        items_level<kEq>(sm, 1, kb, a, tid);
         const double* s = sm.scl + (kb & 1) * AF::NSCALE;
-        b3c = s[AF::NXP + xi];
-        b6c = s[2 * AF::NXP + AF::NYP + yi];
+        b3c = s[b3_off<kEq>() + xi];
+        b6c = s[b6_off<kEq>() + yi];
     }
     abort = __syncthreads_or(bad);
 
@@ -341,8 +361,14 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
         const double p7 = __fma_rn(lwe, wc, -__dmul_rn(lwc, we));
         xu = __dadd_rn(xu, p7);
         xu = __dadd_rn(xu, p7m);
-        const double yu = __fma_rn(LU[c0 + AF::BX], iy[kF2 * AF::NYP + yi],
-                                   -__dmul_rn(LU[c0 - AF::BX], iy[kF2 * AF::NYP + yi - AF::YW]));
+        double yu = 0.0;
+        if (kSameT) {  // one coefficient for the x and y parts
+            xu = __fma_rn(LU[c0 + AF::BX], iy[kF2 * AF::NYP + yi], xu);
+            xu = __fma_rn(-LU[c0 - AF::BX], iy[kF2 * AF::NYP + yi - AF::YW], xu);
+        } else {
+            yu = __fma_rn(LU[c0 + AF::BX], iy[kF2 * AF::NYP + yi],
+                          -__dmul_rn(LU[c0 - AF::BX], iy[kF2 * AF::NYP + yi - AF::YW]));
+        }
         const double f3 = __dadd_rn(wc, we);
         const double zu = __fma_rn(sa[xi], f3, -__dmul_rn(b3m, f3m));
 
@@ -354,16 +380,28 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
         const double p8 = __fma_rn(lwn, wc, -__dmul_rn(lwc, wn));
         yv = __dadd_rn(yv, p8);
         yv = __dadd_rn(yv, p8m);
-        const double xv = __fma_rn(LV[c0 + 1], ix[kF4 * AF::NXP + xi],
-                                   -__dmul_rn(LV[c0 - 1], ix[kF4 * AF::NXP + xi - 1]));
+        double xv = 0.0;
+        if (kSameT) {
+            yv = __fma_rn(LV[c0 + 1], ix[kF4 * AF::NXP + xi], yv);
+            yv = __fma_rn(-LV[c0 - 1], ix[kF4 * AF::NXP + xi - 1], yv);
+        } else {
+            xv = __fma_rn(LV[c0 + 1], ix[kF4 * AF::NXP + xi], -__dmul_rn(LV[c0 - 1], ix[kF4 * AF::NXP + xi - 1]));
+        }
         const double f6 = __dadd_rn(wc, wn);
         const double zv = __fma_rn(sa[2 * AF::NXP + yi], f6, -__dmul_rn(b6m, f6m));
 
         // gw: x (sw-x), y (sw-y), z (sw-z, F of su-z and sv-z)
-        const double xw = __fma_rn(lwe, ix[kF7 * AF::NXP + xi], -__dmul_rn(lww, ix[kF7 * AF::NXP + xi - 1]));
-        const double yw = __fma_rn(lwn, iy[kF8 * AF::NYP + yi], -__dmul_rn(lws, iy[kF8 * AF::NYP + yi - AF::YW]));
+        double xw = __fma_rn(lwe, ix[kF7 * AF::NXP + xi], -__dmul_rn(lww, ix[kF7 * AF::NXP + xi - 1]));
+        double yw = 0.0;
+        if (kSameT) {
+            xw = __fma_rn(lwn, iy[kF8 * AF::NYP + yi], xw);
+            xw = __fma_rn(-lws, iy[kF8 * AF::NYP + yi - AF::YW], xw);
+        } else {
+            yw = __fma_rn(lwn, iy[kF8 * AF::NYP + yi], -__dmul_rn(lws, iy[kF8 * AF::NYP + yi - AF::YW]));
+        }
         const double a9 = __dmul_rn(coef_at(a.tzd1, k + 1, nz), lwk);
-        const double b9 = __dmul_rn(coef_at(a.tzd2, k, nz), lwc);
+        // kEq: tzd2(k) gsw(k) = tzd1(k) gsw(k), formed one step earlier
+        const double b9 = kEq ? a9c : __dmul_rn(coef_at(a.tzd2, k, nz), lwc);
         const double f9 = __dadd_rn(wc, wk);
         const double p9 = __fma_rn(a9, wc, -__dmul_rn(b9, wk));
         double zw = __dadd_rn(ix[kP3 * AF::NXP + xi], ix[kP3 * AF::NXP + xi - 1]);
@@ -374,9 +412,16 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
         zw = __dadd_rn(zw, p9);
         zw = __dadd_rn(zw, p9m);
 
-        const double ru = __fma_rn(tcx, xu, __fma_rn(tcy, yu, zu));
-        const double rv = __fma_rn(tcx, xv, __fma_rn(tcy, yv, zv));
-        const double rw = __fma_rn(tcx, xw, __fma_rn(tcy, yw, zw));
+        double ru, rv, rw;
+        if (kSameT) {
+            ru = __fma_rn(tcx, xu, zu);
+            rv = __fma_rn(tcx, yv, zv);
+            rw = __fma_rn(tcx, xw, zw);
+        } else {
+            ru = __fma_rn(tcx, xu, __fma_rn(tcy, yu, zu));
+            rv = __fma_rn(tcx, xv, __fma_rn(tcy, yv, zv));
+            rw = __fma_rn(tcx, xw, __fma_rn(tcy, yw, zw));
+        }
         if (act) {
             if (a.accumulate) {
                 gu[g] += ru;
@@ -395,12 +440,13 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
         f9m = f9;
         p9m = p9;
         b9m = b9;
+        a9c = a9;
         b3m = b3c;
         b6m = b6c;
 
         if (k + 1 < ke) {
             // ---- scale level k+2 (load r+3) into the slot level k used
-            scale_level(sm, r + 3, k + 2, a, tid);
+            scale_level<kEq>(sm, r + 3, k + 2, a, tid);
             abort = __syncthreads_or(bad);  // load r+1 (level k) is free
             if (!abort && tid == 0 && issued < nseq) {
                 fence_proxy_async_smem();
@@ -415,10 +461,10 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
             }
             // ---- items of level k+1 (loads r+2, r+3)
             if (!abort) {
-                items_level(sm, r + 2, k + 1, a, tid);
+                items_level<kEq>(sm, r + 2, k + 1, a, tid);
                 const double* s = sm.scl + ((k + 1) & 1) * AF::NSCALE;
-                b3c = s[AF::NXP + xi];
-                b6c = s[2 * AF::NXP + AF::NYP + yi];
+                b3c = s[b3_off<kEq>() + xi];
+                b6c = s[b6_off<kEq>() + yi];
             }
             abort = __syncthreads_or(bad);
         }
@@ -429,6 +475,42 @@ __global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_consta
     }
 }
 
+// One launch: CTAs [0, sched.items) each take one work item (a level chunk
+// of one tile, in the order of the one-shot schedule); the CTAs after them
+// gather the halo cells, one per thread, filling the schedule's last wave.
+// kSameT (tcx = tcy) is chosen on the host, equal vertical coefficients per
+// CTA from the coefficient arrays.
+template <bool kSameT>
+__global__ void __launch_bounds__(kNT, 2) adjoint_f64_kernel(const __grid_constant__ AdjF64Maps maps, const AdjArgs a,
+                                                             const ItemSched sched) {
+    extern __shared__ unsigned char smem_raw[];
+    const int tid = threadIdx.x;
+    if ((long long)blockIdx.x >= sched.items) {  // CTA-uniform
+        adjoint_halo_cell<double>(a, ((long long)blockIdx.x - sched.items) * kNT + tid);
+        return;
+    }
+    Smem sm;
+    sm.setup(smem_raw);
+    int bx, by, kb, ke;
+    sched_item(sched, a.nz, blockIdx.x, &bx, &by, &kb, &ke);
+    if (vertical_pairs_equal(a, tid)) adjoint_tile<true, kSameT>(maps, a, sm, bx, by, kb, ke, tid);
+    else adjoint_tile<false, kSameT>(maps, a, sm, bx, by, kb, ke, tid);
+}
+
+template <bool kSameT>
+cudaError_t launch_adjoint_f64_t(const AdjF64Maps& m, const AdjArgs& a, cudaStream_t st) {
+    auto kern = adjoint_f64_kernel<kSameT>;
+    const int tx = (a.nx + kTX - 1) / kTX, ty = (a.ny + kTY - 1) / kTY;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, AF::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    ItemSched sched;
+    if ((e = choose_sched(kern, kNT, AF::SMEM_BYTES, tx, ty, a.nz, &sched)) != cudaSuccess) return e;
+    const long long halo = (long long)(2 * (a.ny + 2) + 2 * a.nx) * a.nz;
+    const long long grid = sched.items + (halo + kNT - 1) / kNT;
+    kern<<<(unsigned)grid, kNT, AF::SMEM_BYTES, st>>>(m, a, sched);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 TileShape adjoint_f64_shape() { return TileShape{kTX, kTY, AF::BX, AF::BY, AF::SMEM_BYTES, kNT}; }
@@ -436,15 +518,7 @@ TileShape adjoint_f64_shape() { return TileShape{kTX, kTY, AF::BX, AF::BY, AF::S
 cudaError_t launch_adjoint_f64(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st) {
     AdjF64Maps m;
     for (int f = 0; f < kFields; ++f) m.m[f] = maps6[f];
-    const int tx = (a.nx + kTX - 1) / kTX, ty = (a.ny + kTY - 1) / kTY;
-    cudaError_t e = cudaFuncSetAttribute(adjoint_f64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, AF::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    ItemSched sched;
-    if ((e = choose_sched(adjoint_f64_kernel, kNT, AF::SMEM_BYTES, tx, ty, a.nz, &sched)) != cudaSuccess) return e;
-    const long long halo = (long long)(2 * (a.ny + 2) + 2 * a.nx) * a.nz;
-    const long long grid = sched.items + (halo + kNT - 1) / kNT;
-    adjoint_f64_kernel<<<(unsigned)grid, kNT, AF::SMEM_BYTES, st>>>(m, a, sched);
-    return cudaGetLastError();
+    return a.tcx == a.tcy ? launch_adjoint_f64_t<true>(m, a, st) : launch_adjoint_f64_t<false>(m, a, st);
 }
 
 cudaError_t read_and_clear_status_adjoint_f64(unsigned int* status, cudaStream_t st) {

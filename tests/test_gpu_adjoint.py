@@ -71,6 +71,34 @@ def test_adjoint_matches_oracle(gpu, oracle_lib, mode, dtype_name, shape, aligne
         assert np.max(np.abs(gn - wn)) <= tol * scale, (name, np.max(np.abs(gn - wn)) / scale)
 
 
+@pytest.mark.parametrize("dy", [50.0, 40.0])
+@pytest.mark.parametrize("density", [False, True])
+def test_adjoint_f64_shared_product_paths(gpu, oracle_lib, dy, density):
+    """The native FP64 adjoint shares products when tcx = tcy (one
+    coefficient for an output's x and y parts) and when every level's two
+    vertical coefficients are equal (no density: one scaled cotangent per
+    cell for both faces). All four combinations against the oracle."""
+    from paper_2107_13500_gb300 import pw
+    torch = gpu
+    nx, ny, nz = 45, 21, 12
+    dz = synth.dz_stretched(nz)
+    rho, rhon = synth.density_exponential(dz) if density else (None, None)
+    u, v, w = synth.fields_iid(nx, ny, nz, seed=71)
+    gs = [_raw(nx, ny, nz, 72, s) for s in range(3)]
+    ref = oracle_lib.advect_adjoint(u, v, w, oracle_lib.coeffs(nz, 50.0, dy, dz, rho, rhon), nx, ny, *gs)
+    c = pw.make_coeffs(nz, 50.0, dy, dz, rho, rhon).to_device()
+    x = [to_device(a, nx, torch.float64) for a in (u, v, w)]
+    g = [to_device(a, nx, torch.float64) for a in gs]
+    out = pw.advect_adjoint(*x, c, nx, ny, *g, mode="f64")
+    torch.cuda.synchronize()
+    assert pw.device_status() == 0
+    for name, got, want in zip(("gu", "gv", "gw"), out, ref):
+        gn = got.double().cpu().numpy()[:, :, : nx + 2]
+        wn = want[:, :, : nx + 2]
+        err = np.max(np.abs(gn - wn)) / np.max(np.abs(wn))
+        assert err <= 1e-13, (name, err)
+
+
 @pytest.mark.parametrize("mode", ["f64", "paired"])
 def test_adjoint_accumulate(gpu, mode):
     from paper_2107_13500_gb300 import pw
