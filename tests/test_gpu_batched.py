@@ -22,15 +22,20 @@ def gpu():
     return torch
 
 
-def _domains(torch, sizes, mode, seed=10, aligned=True):
+def _domains(torch, sizes, mode, seed=10, aligned=True, mixed=False):
     """One domain per (nx, ny, nz): stretched grid, smooth winds; FP32 modes
-    get float fields (split: perturbations and the level table)."""
+    get float fields (split: perturbations and the level table). `mixed`
+    gives every third domain dy = 40 m and every third, from the second, a
+    density profile, so one batch holds domains on both arithmetic forms of
+    the kernels (shared coefficient products, or each term on its own)."""
     from paper_2107_13500_gb300 import pw
     doms = []
     for n, (nx, ny, nz) in enumerate(sizes):
         dz = synth.dz_stretched(nz)
-        c = pw.make_coeffs(nz, 50.0, 50.0, dz).to_device()
-        u, v, w = synth.fields_modes(nx, ny, nz, 50.0, 50.0, dz, seed=seed + n, n_modes=3)
+        dy = 40.0 if mixed and n % 3 == 0 else 50.0
+        rho, rhon = synth.density_exponential(dz) if mixed and n % 3 == 1 else (None, None)
+        c = pw.make_coeffs(nz, 50.0, dy, dz, rho, rhon).to_device()
+        u, v, w = synth.fields_modes(nx, ny, nz, 50.0, dy, dz, seed=seed + n, n_modes=3)
         if mode in ("paired", "f64"):
             f = [to_device(a, nx, torch.float64, aligned=aligned) for a in (u, v, w)]
             d = dict(u=f[0], v=f[1], w=f[2], nx=nx, ny=ny, coeffs=c)
@@ -60,7 +65,7 @@ SMALL = [(37, 13, 5), (64, 8, 3), (130, 33, 17), (5, 70, 2), (96, 96, 40), (1, 1
 def test_batched_equals_single(gpu, mode, aligned):
     from paper_2107_13500_gb300 import pw
     torch = gpu
-    doms = _domains(torch, SMALL, mode, aligned=aligned)
+    doms = _domains(torch, SMALL, mode, aligned=aligned, mixed=True)
     ref = _one_by_one(pw, doms, mode)
     for v in range(pw.variant_count(mode)):
         b = pw.Batch(doms, mode, v)

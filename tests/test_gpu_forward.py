@@ -65,20 +65,24 @@ def test_ragged_stretched_density(gpu, oracle_lib, mode, shape, aligned):
     check_mode(mode, g, o, *a, nx, ny)
 
 
+@pytest.mark.parametrize("dy", [50.0, 45.0])
 @pytest.mark.parametrize("case", ["equal", "density", "one_level_differs"])
-def test_f64_vertical_coefficient_paths(gpu, oracle_lib, case):
-    """The native FP64 kernel shares one coefficient product between a
+@pytest.mark.parametrize("mode", F64_MODES)
+def test_f64_vertical_coefficient_paths(gpu, oracle_lib, mode, case, dy):
+    """Both FP64-class kernels share one coefficient product between a
     level's two vertical face terms when every level's lower and upper
-    coefficients are equal (no density stratification), and scales each face
-    sum on its own otherwise. Both, and a grid equal on every level but one
-    (which must take the general form), against the oracle on the same
-    coefficients at the strict per-point scale."""
+    coefficients are equal (no density stratification), and scale each face
+    sum on its own otherwise; the paired kernel shares that form only where
+    tcx = tcy as well (dx = dy), and then also takes one coefficient product
+    for an output's x and y parts. Every combination, and a grid equal on
+    every level but one (which must take the general form), against the
+    oracle on the same coefficients at the mode's own scale."""
     from paper_2107_13500_gb300 import pw
     torch = gpu
     nx, ny, nz = 70, 19, 13
     dz = synth.dz_stretched(nz)
     rho, rhon = synth.density_exponential(dz) if case == "density" else (None, None)
-    c = pw.make_coeffs(nz, 50.0, 45.0, dz, rho, rhon)
+    c = pw.make_coeffs(nz, 50.0, dy, dz, rho, rhon)
     if case == "one_level_differs":
         c.tz4[1, 6] *= 1.5  # tzc2 of one level
         c.tz4[3, 4] *= 0.5  # tzd2 of another
@@ -89,12 +93,13 @@ def test_f64_vertical_coefficient_paths(gpu, oracle_lib, case):
     c.to_device()
     u, v, w = synth.fields_iid(nx, ny, nz, seed=91)
     (so, ab) = oracle_lib.advect(u, v, w, co, nx, ny, want_abs=True, nthreads=8)
+    mb = oracle_lib.monomial_scale(u, v, w, co, nx, ny, nthreads=8) if mode == "paired" else None
     du, dv, dw = (to_device(f, nx, torch.float64) for f in (u, v, w))
-    out = pw.advect(du, dv, dw, c, nx, ny, mode="f64")
+    out = pw.advect(du, dv, dw, c, nx, ny, mode=mode)
     torch.cuda.synchronize()
     assert pw.device_status() == 0
     g = [to_numpy_f64(t, u.shape[2], nx) for t in out]
-    check_mode("f64", g, so, ab, None, nx, ny)
+    check_mode(mode, g, so, ab, mb, nx, ny)
 
 
 @pytest.mark.parametrize("mode", F64_MODES)
