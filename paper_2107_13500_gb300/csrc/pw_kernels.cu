@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "pw_common.cuh"
+#include "pw_dadd.cuh"
 #include "pw_internal.h"
 #include "pw_pair.cuh"
 #include "pw_ring.cuh"
@@ -71,15 +72,24 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 // order), since float pairs cannot carry it.
 //
 // split_pert_kernel: a flat grid over every cell (halo included) writes
-// float(f - mean[k]): one FP64 subtraction, then the round-to-nearest-even
-// conversion to float by integer operations (the hardware conversion issues
-// on the FP64 pipe too), which gives the hardware's result bit for bit; the
-// values outside the normal float range take the hardware conversion. The
+// float(f - mean[k]): one FP64 subtraction (one row in kPertRows by the
+// exact integer adder of pw_dadd.cuh, so that the ALU shares the FP64
+// pipe's load), then the round-to-nearest-even conversion to float by
+// integer operations (the hardware conversion issues on the FP64 pipe too),
+// which gives the hardware's result bit for bit; the values outside the
+// normal float range take the hardware conversion. The
 // levels are walked top down, the reverse of the mean pass, so the levels
 // that pass read last are read again while they are still in L2.
 
 constexpr int kSplitThreads = 512, kSplitCluster = 8, kSplitUnroll = 16;
 constexpr int kPertThreads = 128, kPertRows = 8;  // columns per CTA, rows per thread
+// Rows of each kPertRows group whose subtraction runs on the integer ALU
+// (exact binary64 addition of -mean) instead of the FP64 pipe: the two pipes
+// then work side by side.
+#ifndef PW_PERT_INT_ROWS
+#define PW_PERT_INT_ROWS 1
+#endif
+constexpr int kPertIntRows = PW_PERT_INT_ROWS;
 
 // Biased double exponents of the magnitudes the paired sum carries: [2^-60, 2^100).
 constexpr unsigned kPairExpLo = 1023 - 60, kPairExpHi = 1023 + 100;
@@ -209,6 +219,12 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
     }
 }
 
+// The FP64 subtraction for lanes dadd_int refused, out of line so that the
+// common path carries no FP64 instruction.
+__device__ __noinline__ double dsub_refused(double x, double m, double d, bool ok) {
+    return ok ? d : __dsub_rn(x, m);
+}
+
 // Thread x of CTA (bx, by, bz) converts column bx*kPertThreads + x of the
 // row chunks by, by + gridDim.y, ... (kPertRows rows each) of levels
 // nz-1-bz, nz-1-bz-gridDim.z, ... (top down).
@@ -219,6 +235,7 @@ __global__ void __launch_bounds__(kPertThreads)
     if (i > nx + 1) return;
     for (int k = nz - 1 - (int)blockIdx.z; k >= 0; k -= (int)gridDim.z) {
         const double m = __ldg(mean + k);
+        const double neg_m = __hiloint2double(__double2hiint(m) ^ (int)0x80000000, __double2loint(m));
         for (int j0 = blockIdx.y * kPertRows; j0 < ny + 2; j0 += gridDim.y * kPertRows) {
             const double* col = f + (size_t)k * (size_t)fsz + (size_t)j0 * (size_t)fsy + i;
             float* ocol = fp + (size_t)k * (size_t)psz + (size_t)j0 * (size_t)psy + i;
@@ -232,7 +249,16 @@ __global__ void __launch_bounds__(kPertThreads)
                 }
 #pragma unroll
                 for (int q = 0; q < kPertRows; ++q) {
-                    *ocol = double_to_float_rn(__dsub_rn(x[q], m));
+                    double d;
+                    if (q < kPertIntRows) {
+                        // the same difference on the integer ALU; the FP64
+                        // unit only for the lanes it refuses
+                        const bool ok = dadd_int(x[q], neg_m, &d);
+                        if (__any_sync(__activemask(), !ok)) d = dsub_refused(x[q], m, d, ok);
+                    } else {
+                        d = __dsub_rn(x[q], m);
+                    }
+                    *ocol = double_to_float_rn(d);
                     ocol += psy;
                 }
             } else {
