@@ -161,9 +161,11 @@ int pw_make_split_table(int nz, double tcx, double tcy, const double *tz4_host,
  * fp = float(f - mean[k]) on every cell of the level including the halo
  * (the FP64 difference rounded to nearest even, bit for bit the hardware's
  * conversion). The means are summed in a fixed order, so they repeat from
- * call to call: in paired FP32 (about 48 significant bits; error at most a
- * few hundred units of 2^-48 of the mean magnitude) when every interior
- * value is 0 or lies in [2^-60, 2^100), else in FP64. Any value near the
+ * call to call: in bands of 16 rows, part of each band in FP64 and the rest
+ * in paired FP32 (about 48 significant bits; error at most a few hundred
+ * units of 2^-48 of the mean magnitude), when the pair-summed values and the
+ * FP64 parts are 0 or lie in [2^-60, 2^100); else the level in FP64. The
+ * band sums pass through cells of fp before fp is written. Any value near the
  * average serves the split, since pw_make_split_table and the
  * perturbations use the same stored mean. f uses dims_f (double), fp uses
  * dims_p (float; same nx, ny, nz). mean is a DEVICE array of nz doubles.

@@ -5,7 +5,6 @@
 // pw_adjoint.cu.
 #include <cuda.h>
 #include <cuda_runtime.h>
-#include <cooperative_groups.h>
 #include <stdint.h>
 
 #include "pw_common.cuh"
@@ -16,7 +15,6 @@
 
 namespace pw {
 
-namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // Periodic halo fill: x halo on rows 1..ny, then the full rows 0 and ny+1.
@@ -61,15 +59,22 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 // FP64 pipe (about two FP64 lane operations per clock per SM on GB300) so
 // that both are bound by HBM.
 //
-// split_mean_kernel: a cluster of kSplitCluster CTAs takes one level. Each
-// thread sums its share of the interior (a fixed set of columns, rows in
-// order) in paired FP32 -- each double split into a float pair by integer
-// operations, pairs added with TwoSum -- then a fixed shuffle tree per warp,
-// the warps in order, and rank 0 adds the cluster's partial sums in rank
-// order through distributed shared memory, so the mean does not depend on
-// scheduling. A level holding a nonzero magnitude outside [2^-60, 2^100), an
-// infinity or a NaN is summed again in FP64 by the same cluster (same fixed
-// order), since float pairs cannot carry it.
+// split_sum_kernel: a flat grid of CTAs, one per (row band, level): the
+// interior of level k is cut into nbands bands of about kSumRows rows. Each
+// thread sums its share of a band (a fixed set of columns, rows in order) in
+// paired FP32 -- each double split into a float pair by integer operations,
+// pairs added with TwoSum -- then a fixed shuffle tree per warp and the
+// warps in order; thread 0 stores the band's pair and a flag (every value
+// summable as a pair) in three cells of the perturbation output's level k,
+// which split_pert_kernel overwrites afterwards. Small CTAs over every SM
+// keep enough loads in flight to stream the field at HBM rate.
+//
+// split_reduce_kernel: one CTA per level adds the band sums in a fixed
+// order (lane l of the first warp the bands l, l+32, ... in turn, then a
+// fixed shuffle tree), so the mean does not depend on scheduling. A level
+// where a pair-summed value or an FP64 part lies outside [2^-60, 2^100)
+// (zero excepted), or is infinite or NaN, is summed again wholly in FP64 by
+// that CTA (a fixed order too), since float pairs cannot carry it.
 //
 // split_pert_kernel: a flat grid over every cell (halo included) writes
 // float(f - mean[k]): one FP64 subtraction (one row in kPertRows by the
@@ -81,7 +86,19 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 // levels are walked top down, the reverse of the mean pass, so the levels
 // that pass read last are read again while they are still in L2.
 
-constexpr int kSplitThreads = 512, kSplitCluster = 8, kSplitUnroll = 16;
+#ifndef PW_SUM_THREADS
+#define PW_SUM_THREADS 128
+#endif
+#ifndef PW_SUM_ROWS
+#define PW_SUM_ROWS 16
+#endif
+#ifndef PW_SUM_F64_ROWS
+#define PW_SUM_F64_ROWS 8
+#endif
+constexpr int kSumThreads = PW_SUM_THREADS, kSumRows = PW_SUM_ROWS;  // threads; rows per band at most (the loads in flight per column)
+// Rows of each band summed in FP64 (the FP64 pipe is otherwise idle here)
+// rather than in paired FP32 (about 20 issue slots per value).
+constexpr int kSum64Rows = PW_SUM_F64_ROWS;
 constexpr int kPertThreads = 128, kPertRows = 8;  // columns per CTA, rows per thread
 // Rows of each kPertRows group whose subtraction runs on the integer ALU
 // (exact binary64 addition of -mean) instead of the FP64 pipe: the two pipes
@@ -121,50 +138,51 @@ __device__ __forceinline__ float double_to_float_rn(double d) {
     return __double2float_rn(d);
 }
 
-__global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitThreads)
-    split_mean_kernel(const double* __restrict__ f, long long fsy, long long fsz, int nx, int ny, int nz,
-                      double* __restrict__ mean) {
-    __shared__ float2 warp_part[kSplitThreads / 32];
-    __shared__ double warp_part64[kSplitThreads / 32];
-    __shared__ float2 cta_sum;
-    __shared__ double cta_sum64;
-    __shared__ int cta_ok;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int rank = (int)cluster.block_rank();
+// Cell n (row-major over the (ny+2) x (nx+2) cells, halo included) of the
+// perturbation output's level k: the band sums' scratch slots.
+__device__ __forceinline__ float* sum_slot(float* fp, long long psy, long long psz, int nx, int k, int n) {
+    const int w = nx + 2, r = n / w, c = n - r * w;
+    return fp + (size_t)k * (size_t)psz + (size_t)r * (size_t)psy + c;
+}
+
+__global__ void __launch_bounds__(kSumThreads)
+    split_sum_kernel(const double* __restrict__ f, long long fsy, long long fsz, int nx, int ny, int nz, int nbands,
+                     float* __restrict__ fp, long long psy, long long psz) {
+    __shared__ float2 warp_part[kSumThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // interior rows [r0, r1) of this CTA
-    const int r0 = 1 + (int)((long long)ny * rank / kSplitCluster);
-    const int r1 = 1 + (int)((long long)ny * (rank + 1) / kSplitCluster);
-    // the whole cluster walks the same levels
+    const int b = blockIdx.x;
+    // interior rows [r0, r1) of band b
+    const int r0 = 1 + (int)((long long)ny * b / nbands);
+    const int r1 = 1 + (int)((long long)ny * (b + 1) / nbands);
     for (int k = blockIdx.y; k < nz; k += gridDim.y) {
         const double* lev = f + (size_t)k * (size_t)fsz;
         pf s = {0.0f, 0.0f};
+        double s64 = 0.0;  // the first kSum64Rows rows of each column, on the FP64 pipe
         bool ok = true;
-        for (int i = 1 + tid; i <= nx; i += kSplitThreads) {
+        for (int i = 1 + tid; i <= nx; i += kSumThreads) {
             // rows advance by adding the stride: 64-bit integer products
             // would issue on the FP64 pipe
+            // a band has at most kSumRows rows: all its loads in flight at once
             const double* p = lev + i + (size_t)r0 * (size_t)fsy;
-            int j = r0;
-            for (; j + kSplitUnroll <= r1; j += kSplitUnroll) {
-                double x[kSplitUnroll];
+            double x[kSumRows];
 #pragma unroll
-                for (int q = 0; q < kSplitUnroll; ++q) {
-                    x[q] = __ldg(p);
-                    p += fsy;
-                }
+            for (int q = 0; q < kSumRows; ++q) {
+                x[q] = (r0 + q < r1) ? __ldg(p) : 0.0;
+                p += fsy;
+            }
 #pragma unroll
-                for (int q = 0; q < kSplitUnroll; ++q) {
+            for (int q = 0; q < kSumRows; ++q) {
+                if (q < kSum64Rows) {
+                    s64 = __dadd_rn(s64, x[q]);  // rows past the band add zeros
+                } else if (r0 + q < r1) {
                     ok &= pair_summable(x[q]);
                     s = padd(s, split_double(x[q]));
                 }
             }
-            for (; j < r1; ++j) {
-                const double x = __ldg(p);
-                p += fsy;
-                ok &= pair_summable(x);
-                s = padd(s, split_double(x));
-            }
         }
+        // the FP64 part joins the pair sum (it must lie in the pairs' range)
+        ok &= pair_summable(s64);
+        s = padd(s, split_double(s64));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const pf t = {__shfl_xor_sync(0xffffffffu, s.h, o), __shfl_xor_sync(0xffffffffu, s.l, o)};
@@ -174,28 +192,45 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
         const int all_ok = __syncthreads_and(ok);
         if (tid == 0) {
             pf t = {0.0f, 0.0f};
-            for (int q = 0; q < kSplitThreads / 32; ++q) t = padd(t, pf{warp_part[q].x, warp_part[q].y});
-            cta_sum = make_float2(t.h, t.l);
-            cta_ok = all_ok;
+            for (int q = 0; q < kSumThreads / 32; ++q) t = padd(t, pf{warp_part[q].x, warp_part[q].y});
+            *sum_slot(fp, psy, psz, nx, k, 3 * b) = t.h;
+            *sum_slot(fp, psy, psz, nx, k, 3 * b + 1) = t.l;
+            *sum_slot(fp, psy, psz, nx, k, 3 * b + 2) = __int_as_float(all_ok);
         }
-        cluster.sync();  // every CTA's partial sum and flag is in place
-        bool level_ok = true;
-        for (int q = 0; q < kSplitCluster; ++q) level_ok &= (*cluster.map_shared_rank(&cta_ok, q) != 0);
-        if (level_ok) {
-            if (rank == 0 && tid == 0) {
+        __syncthreads();  // warp_part is rewritten for the next level
+    }
+}
+
+__global__ void __launch_bounds__(kSumThreads)
+    split_reduce_kernel(const double* __restrict__ f, long long fsy, long long fsz, int nx, int ny, int nz, int nbands,
+                        const float* __restrict__ fp, long long psy, long long psz, double* __restrict__ mean) {
+    __shared__ double warp_part64[kSumThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float* slots = const_cast<float*>(fp);
+    for (int k = blockIdx.x; k < nz; k += gridDim.x) {
+        bool ok = true;
+        for (int b = tid; b < nbands; b += kSumThreads) ok &= __float_as_int(*sum_slot(slots, psy, psz, nx, k, 3 * b + 2)) != 0;
+        if (__syncthreads_and(ok)) {
+            if (warp == 0) {
+                // lane l adds bands l, l+32, ... in order, then a fixed tree
                 pf t = {0.0f, 0.0f};
-                for (int q = 0; q < kSplitCluster; ++q) {
-                    const float2 c = *cluster.map_shared_rank(&cta_sum, q);
-                    t = padd(t, pf{c.x, c.y});
+                for (int b = lane; b < nbands; b += 32)
+                    t = padd(t, pf{*sum_slot(slots, psy, psz, nx, k, 3 * b), *sum_slot(slots, psy, psz, nx, k, 3 * b + 1)});
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const pf u = {__shfl_xor_sync(0xffffffffu, t.h, o), __shfl_xor_sync(0xffffffffu, t.l, o)};
+                    t = padd(t, u);
                 }
-                mean[k] = ((double)t.h + (double)t.l) / ((double)nx * (double)ny);
+                if (lane == 0) mean[k] = ((double)t.h + (double)t.l) / ((double)nx * (double)ny);
             }
         } else {
-            // values the pairs cannot carry: the level in FP64, same order
+            // values the pairs cannot carry: the level in FP64, columns
+            // strided over the threads, rows in order, warps in order
+            const double* lev = f + (size_t)k * (size_t)fsz;
             double s64 = 0.0;
-            for (int i = 1 + tid; i <= nx; i += kSplitThreads) {
-                const double* p = lev + i + (size_t)r0 * (size_t)fsy;
-                for (int j = r0; j < r1; ++j, p += fsy) s64 += __ldg(p);
+            for (int i = 1 + tid; i <= nx; i += kSumThreads) {
+                const double* p = lev + i + (size_t)fsy;
+                for (int j = 1; j <= ny; ++j, p += fsy) s64 += __ldg(p);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s64 += __shfl_xor_sync(0xffffffffu, s64, o);
@@ -203,19 +238,11 @@ __global__ void __cluster_dims__(kSplitCluster, 1, 1) __launch_bounds__(kSplitTh
             __syncthreads();
             if (tid == 0) {
                 double t = 0.0;
-                for (int q = 0; q < kSplitThreads / 32; ++q) t += warp_part64[q];
-                cta_sum64 = t;
-            }
-            cluster.sync();
-            if (rank == 0 && tid == 0) {
-                double t = 0.0;
-                for (int q = 0; q < kSplitCluster; ++q) t += *cluster.map_shared_rank(&cta_sum64, q);
+                for (int q = 0; q < kSumThreads / 32; ++q) t += warp_part64[q];
                 mean[k] = t / ((double)nx * (double)ny);
             }
         }
-        // rank 0 has read every partial sum before any CTA rewrites its own
-        // (next level) or leaves
-        cluster.sync();
+        __syncthreads();  // warp_part64 and the flags are read before the next level
     }
 }
 
@@ -271,9 +298,14 @@ __global__ void __launch_bounds__(kPertThreads)
 cudaError_t launch_split_field(const double* f, long long fsy, long long fsz, float* fp, long long psy,
                                long long psz, int nx, int ny, int nz, double* mean, cudaStream_t st) {
     const unsigned gz = (unsigned)(nz < 65535 ? nz : 65535);  // grid y/z limit; the kernels loop over levels
-    split_mean_kernel<<<dim3(kSplitCluster, gz), kSplitThreads, 0, st>>>(f, fsy, fsz, nx, ny, nz, mean);
+    // bands of at most kSumRows rows; their 3 scratch cells per band fit in
+    // a level of the output (3 ceil(ny/kSumRows) <= 3 ny < (ny+2)(nx+2))
+    const int nbands = (ny + kSumRows - 1) / kSumRows;
+    split_sum_kernel<<<dim3((unsigned)nbands, gz), kSumThreads, 0, st>>>(f, fsy, fsz, nx, ny, nz, nbands, fp, psy, psz);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    split_reduce_kernel<<<gz, kSumThreads, 0, st>>>(f, fsy, fsz, nx, ny, nz, nbands, fp, psy, psz, mean);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const int chunks = (ny + 2 + kPertRows - 1) / kPertRows;
     const dim3 grid((unsigned)((nx + 2 + kPertThreads - 1) / kPertThreads), (unsigned)(chunks < 65535 ? chunks : 65535),
                     gz);

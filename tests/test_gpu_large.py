@@ -127,10 +127,12 @@ def test_split_beyond_2_31_elements(gpu, oracle_lib):
     fp, means = zip(*(pw.split_field(t, NX, NY) for t in x))
     torch.cuda.synchronize()
     assert pw.device_status() == 0
-    # paired sums of at most per_thread + 23 additions, each within 2^-47 of
-    # the magnitudes summed so far (|f| <= 10)
-    per_thread = -(-NX // 256) * -(-NY // 8)
-    bound = (per_thread + 23) * 2.0 ** -47 * 10.0
+    # paired sums of at most n_add additions on a value's path (a thread's
+    # columns of a band of 16 rows, the warp tree, 4 warps, a lane's bands,
+    # the lane tree, the join), each within 2^-47 of the magnitudes summed
+    # so far (|f| <= 10)
+    n_add = -(-NX // 128) * 16 + 5 + 4 + -(-(-(-NY // 16)) // 32) + 5 + 2
+    bound = n_add * 2.0 ** -47 * 10.0
     for t, m in zip(x, means):
         want = t[:, 1:NY + 1, 1:NX + 1].mean(dim=(1, 2))
         assert float((m - want).abs().max()) <= bound

@@ -125,9 +125,11 @@ def test_split_field_means_and_perturbations(gpu):
     """pw_split_field: level means of the interior and float perturbations
     on every cell, halo included. The means are summed in paired FP32 (each
     double split into a float pair of 48 significant bits, pairs added with
-    TwoSum): each of the at most n_add additions on a thread's path (its own
-    cells, the warp tree, the warps, the cluster) errs by at most 2^-47 of
-    the magnitudes summed so far, so |mean - exact| <= n_add 2^-47 mean|f|."""
+    TwoSum): each of the at most n_add additions on a value's path (its
+    thread's columns of a band of at most 16 rows, 128 threads to a band;
+    the warp tree; the 4 warps; a lane's share of the bands; the tree over
+    the lanes; the join) errs by at most 2^-47 of the magnitudes summed so
+    far, so |mean - exact| <= n_add 2^-47 mean|f|."""
     from paper_2107_13500_gb300 import pw
     torch = gpu
     for nx, ny, nz in ((70, 33, 6), (512, 512, 4)):
@@ -138,8 +140,8 @@ def test_split_field_means_and_perturbations(gpu):
         m = mean.cpu().numpy()
         inner = interior(u, nx, ny)
         want = inner.mean(axis=(1, 2))
-        per_thread = -(-nx // 256) * -(-ny // 8)
-        n_add = per_thread + 5 + 8 + 8 + 2
+        bands = -(-ny // 16)
+        n_add = -(-nx // 128) * 16 + 5 + 4 + -(-bands // 32) + 5 + 2
         bound = n_add * 2.0 ** -47 * np.abs(inner).mean(axis=(1, 2))
         assert np.all(np.abs(m - want) <= bound), (np.abs(m - want) / bound)
         p = fp.cpu().numpy()[:, :, : nx + 2].astype(np.float64)
