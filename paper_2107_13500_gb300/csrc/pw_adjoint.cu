@@ -442,8 +442,20 @@ __global__ void fold_halo_x_kernel(T* f, int nx, int ny, int nz, long long sy, l
 #ifndef PW_ADJ_STRIP_TX
 #define PW_ADJ_STRIP_TX 32
 #endif
+#ifndef PW_ADJ_STRIP_CELLS
+#define PW_ADJ_STRIP_CELLS 2
+#endif
 constexpr int kSTX = PW_ADJ_STRIP_TX, kSTY = PW_ADJ_STRIP_TY, kSS = PW_ADJ_STRIP_STAGES;  // cells per tile row, rows, TMA stages
-constexpr int kSNT = (kSTX / 4) * kSTY;       // threads
+// Cells of a row per thread (a strip): 4 or 2. Two cells per thread double
+// the threads of a CTA on the same staged boxes (more warps to hide latency)
+// at the cost of more shared loads per cell.
+constexpr int kStripCells = PW_ADJ_STRIP_CELLS;
+template <int kCells>
+struct StripThreads {
+    static_assert(kCells == 4 || kCells == 2, "strips of 4 or 2 cells");
+    static constexpr int NT = (kSTX / kCells) * kSTY;
+};
+constexpr int kSNT = StripThreads<kStripCells>::NT;  // threads
 constexpr int kSMinBlocks = (227 * 1024) / (kSS * kFields * (((kSTX + 8) * (kSTY + 2) * 4 + 127) / 128 * 128) + 1280);
 struct StripShape {
     static constexpr int BX = kSTX + 8;  // tensor x from X0 - 4 to X0 + kSTX + 3
@@ -459,6 +471,7 @@ struct StripShape {
 
 // Zero the cotangent cells of a staged level that are not computed output
 // points (the paired kernel does the same while it splits a level).
+template <int NT>
 __device__ __forceinline__ void zero_outside_strip(unsigned char* stage, int lev, const AdjArgs& a, int X0, int y0,
                                                    int tid) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -472,7 +485,7 @@ __device__ __forceinline__ void zero_outside_strip(unsigned char* stage, int lev
         const bool lv = (f == 5) ? lev_w : lev_s;
         if (lv && !edge) continue;
         float* box = reinterpret_cast<float*>(stage + f * StripShape::BOX_STRIDE);
-        for (int n = tid; n < StripShape::BX * StripShape::BY; n += kSNT) {
+        for (int n = tid; n < StripShape::BX * StripShape::BY; n += NT) {
             const int r = n / StripShape::BX, b = n - r * StripShape::BX;
             const int i = i0 + b, j = j0 + r;
             if (!lv || i < 1 || i > nx || j < 1 || j > ny) {
@@ -484,23 +497,56 @@ __device__ __forceinline__ void zero_outside_strip(unsigned char* stage, int lev
     if (wrote) fence_proxy_async_smem();
 }
 
-// Columns cc-1 .. cc+4 of a box row (cc 16-byte aligned): v[0] = west of the
-// strip's first cell, v[1..4] = the strip, v[5] = east of its last cell.
-// Only the 16-byte loads whose columns are used are issued.
-template <bool kW, bool kE>
-__device__ __forceinline__ void row6(const float* p, float* v) {
-    const float4 b = *reinterpret_cast<const float4*>(p);
-    v[1] = b.x;
-    v[2] = b.y;
-    v[3] = b.z;
-    v[4] = b.w;
-    if constexpr (kW) v[0] = reinterpret_cast<const float4*>(p)[-1].w;
-    else v[0] = 0.0f;
-    if constexpr (kE) v[5] = reinterpret_cast<const float4*>(p)[1].x;
-    else v[5] = 0.0f;
+// Columns cc-1 .. cc+kCells of a box row (cc aligned to the strip's width
+// in bytes): v[0] = west of the strip's first cell, v[1..kCells] = the
+// strip, v[kCells+1] = east of its last cell. Only the loads whose columns
+// are used are issued.
+template <int kCells, bool kW, bool kE>
+__device__ __forceinline__ void row_strip(const float* p, float* v) {
+    if constexpr (kCells == 4) {
+        const float4 b = *reinterpret_cast<const float4*>(p);
+        v[1] = b.x;
+        v[2] = b.y;
+        v[3] = b.z;
+        v[4] = b.w;
+        if constexpr (kW) v[0] = reinterpret_cast<const float4*>(p)[-1].w;
+        else v[0] = 0.0f;
+        if constexpr (kE) v[5] = reinterpret_cast<const float4*>(p)[1].x;
+        else v[5] = 0.0f;
+    } else {
+        const float2 b = *reinterpret_cast<const float2*>(p);
+        v[1] = b.x;
+        v[2] = b.y;
+        if constexpr (kW) v[0] = p[-1];
+        else v[0] = 0.0f;
+        if constexpr (kE) v[3] = p[2];
+        else v[3] = 0.0f;
+    }
 }
 
-__global__ void __launch_bounds__(kSNT, kSMinBlocks) adjoint_strip_kernel(const __grid_constant__ AdjMaps maps, const AdjArgs a) {
+// The work of a launch as (tile, level) units, tile-major (tile t's levels
+// 0..nz-1 are units t*nz .. t*nz+nz-1), handed to CTAs in one of two ways:
+//   chunks > 0: CTA b takes level chunk b / tiles of tile b % tiles (the
+//     column cut into `chunks` equal chunks, every tile's first chunk first),
+//     so the CTAs in flight read the same levels of neighbouring tiles and
+//     share their halo rows in L2 -- for domains with at least as many tiles
+//     as resident CTAs;
+//   chunks == 0: CTA b takes the run of `len` units from b * len, the end of
+//     one tile's column and the start of the next (or several whole
+//     columns), so that one wave of resident CTAs does equal work however
+//     few the tiles -- for small domains, where uniform chunks leave a
+//     partial second wave.
+struct StripSched {
+    int tiles_x;      // tiles per row of the tile grid
+    int chunks;       // level chunks per tile, or 0 for runs
+    long long total;  // tiles * nz
+    long long len;    // units per CTA (runs)
+};
+
+template <int kCells>
+__global__ void __launch_bounds__(StripThreads<kCells>::NT, kSMinBlocks)
+    adjoint_strip_kernel(const __grid_constant__ AdjMaps maps, const AdjArgs a, const StripSched sch) {
+    constexpr int NT = StripThreads<kCells>::NT;
     constexpr int BX = StripShape::BX;
     extern __shared__ unsigned char smem_raw[];
     __shared__ float coef_s[2][8];  // level coefficients, two levels in flight
@@ -508,28 +554,12 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) adjoint_strip_kernel(const 
     uint64_t* full = reinterpret_cast<uint64_t*>(base + kSS * StripShape::STAGE_BYTES);
 
     const int tid = threadIdx.x;
-    const int tq = tid % (kSTX / 4), ty = tid / (kSTX / 4);
-    const int X0 = blockIdx.x * kSTX, y0 = blockIdx.y * kSTY;
+    const int tq = tid % (kSTX / kCells), ty = tid / (kSTX / kCells);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int i0 = X0 + 4 * tq - a.xoff;  // the strip's first cell (halo included: 0..nx+1)
-    const int j = y0 + ty;
-    const bool row_act = j <= ny + 1;
-    int nact = 0;  // cells of the strip inside 0..nx+1 (a prefix or suffix of the strip)
-    for (int m = 0; m < 4; ++m) nact += (i0 + m >= 0 && i0 + m <= nx + 1) ? 1 : 0;
-    const bool full_strip = row_act && nact == 4 && a.vec;
-    const int bxs = X0 - 4, bys = y0 - 1;  // box start (tensor coordinates), x 16-byte aligned
-    const int kb = (int)((long long)nz * blockIdx.z / gridDim.z);
-    const int ke = (int)((long long)nz * (blockIdx.z + 1) / gridDim.z);
-    const int nseq = ke - kb + 2;  // loads: levels kb-1 .. ke
-
-    auto stage_of = [&](int seq) { return base + (seq % kSS) * StripShape::STAGE_BYTES; };
-    auto issue = [&](int seq, int lev) {
-        uint64_t* bar = &full[seq % kSS];
-        unsigned char* dst = stage_of(seq);
-        mbar_arrive_expect_tx(bar, kFields * StripShape::BOX_BYTES);
-        for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * StripShape::BOX_STRIDE, &maps.m[f], bar, bxs, bys, lev);
-    };
-    auto wait = [&](int seq) { return mbar_wait_bounded(&full[seq % kSS], (uint32_t)((seq / kSS) & 1)); };
+    // loads are numbered per CTA across its tiles: load n uses stage n % kSS
+    // and barrier phase n / kSS
+    auto stage_abs = [&](int n) { return base + (n % kSS) * StripShape::STAGE_BYTES; };
+    auto wait_abs = [&](int n) { return mbar_wait_bounded(&full[n % kSS], (uint32_t)((n / kSS) & 1)); };
 
     if (tid == 0) {
         for (int f = 0; f < kFields; ++f) prefetch_tensormap(&maps.m[f]);
@@ -537,160 +567,219 @@ __global__ void __launch_bounds__(kSNT, kSMinBlocks) adjoint_strip_kernel(const 
         fence_mbar_init();
     }
     __syncthreads();
-    int issued = 0;
-    if (tid == 0)
-        for (; issued < kSS && issued < nseq; ++issued) issue(issued, kb - 1 + issued);
-
-    const int cc = (ty + 1) * BX + 4 + 4 * tq;  // box index of the strip's first cell
-    const float tcx = (float)a.tcx, tcy = (float)a.tcy;
-    float* __restrict__ gu = static_cast<float*>(a.gu);
-    float* __restrict__ gv = static_cast<float*>(a.gv);
-    float* __restrict__ gw = static_cast<float*>(a.gw);
-    size_t g = (size_t)j * (size_t)a.sy + (size_t)(long long)i0 + (size_t)kb * (size_t)a.sz;
-
-    bool bad = false;
-    for (int q = 0; q < 3 && q < nseq; ++q) {
-        const bool ok = wait(q);
-        bad |= !ok;
-        if (ok) zero_outside_strip(stage_of(q), kb - 1 + q, a, X0, y0, tid);
+    int seq0 = 0;  // loads of this CTA's earlier tiles (all issued and consumed)
+    long long unit, unit_end;
+    if (sch.chunks > 0) {
+        const long long tiles = sch.total / nz;
+        const long long c = (long long)blockIdx.x / tiles, t = (long long)blockIdx.x - c * tiles;
+        unit = t * nz + (long long)nz * c / sch.chunks;
+        unit_end = t * nz + (long long)nz * (c + 1) / sch.chunks;
+    } else {
+        unit = (long long)blockIdx.x * sch.len;
+        unit_end = unit + sch.len < sch.total ? unit + sch.len : sch.total;
     }
-    level_coefs<float>(a, kb, tid, coef_s[0]);
-    bool abort = __syncthreads_or(bad);
+    while (unit < unit_end) {
+        const long long t = unit / nz;
+        const int kb = (int)(unit - t * nz);
+        const int ke = (int)(unit_end - t * nz < nz ? unit_end - t * nz : nz);
+        unit = t * nz + ke;
+        const int X0 = (int)(t % sch.tiles_x) * kSTX, y0 = (int)(t / sch.tiles_x) * kSTY;
+        const int i0 = X0 + kCells * tq - a.xoff;  // the strip's first cell (halo included: 0..nx+1)
+        const int j = y0 + ty;
+        const bool row_act = j <= ny + 1;
+        int nact = 0;  // cells of the strip inside 0..nx+1 (a prefix or suffix of the strip)
+        for (int m = 0; m < kCells; ++m) nact += (i0 + m >= 0 && i0 + m <= nx + 1) ? 1 : 0;
+        const bool full_strip = row_act && nact == kCells && a.vec;
+        const int bxs = X0 - 4, bys = y0 - 1;  // box start (tensor coordinates), x 16-byte aligned
+        const int nseq = ke - kb + 2;  // loads: levels kb-1 .. ke
 
-    for (int k = kb; k < ke && !abort; ++k) {
-        const int r = k - kb;
-        const double c_next = (tid < 7 && k + 1 < ke) ? level_coef(a, k + 1, tid) : 0.0;
-        if (r + 3 < nseq) {
-            const bool ok = wait(r + 3);
-            bad |= !ok;
-            if (ok) zero_outside_strip(stage_of(r + 3), k + 2, a, X0, y0, tid);
-        }
-        const unsigned char* Sm = stage_of(r);      // level k-1
-        const unsigned char* S0 = stage_of(r + 1);  // level k
-        const unsigned char* Sp = stage_of(r + 2);  // level k+1
-        auto fld = [&](const unsigned char* st, int f) {
-            return reinterpret_cast<const float*>(st + f * StripShape::BOX_STRIDE) + cc;
+        // load r of this tile (levels kb-1+r) is the CTA's load seq0 + r
+        auto stage_of = [&](int r) { return stage_abs(seq0 + r); };
+        auto wait = [&](int r) { return wait_abs(seq0 + r); };
+        auto issue = [&](int r, int lev) {
+            uint64_t* bar = &full[(seq0 + r) % kSS];
+            unsigned char* dst = stage_of(r);
+            mbar_arrive_expect_tx(bar, kFields * StripShape::BOX_BYTES);
+            for (int f = 0; f < kFields; ++f) tma_load_3d(dst + f * StripShape::BOX_STRIDE, &maps.m[f], bar, bxs, bys, lev);
         };
-        const float* cs = coef_s[r & 1];
-        const float tz1p = cs[0], tz2m = cs[1], tz20 = cs[2], td1p = cs[3], td10 = cs[4], td2m = cs[5], td20 = cs[6];
 
-        // rows: 0 = the strip's row, N = +1, S = -1; index m+1 = cell m,
-        // m = its west neighbour, m+2 = its east neighbour
-        float gu0[6], guN[6], guS[6], gum[6], gup[6];
-        float gv0[6], gvN[6], gvS[6], gvm[6], gvp[6], gvpS[6];
-        float gw0[6], gwN[6], gwS[6], gwm[6], gwmN[6], gwp[6];
-        float u0[6], uN[6], up[6], v0[6], vN[6], vS[6], vp[6], vpS[6], w0[6], wN[6], wm[6], wmN[6], wp[6];
-        row6<true, true>(fld(S0, 3), gu0);
-        row6<true, false>(fld(S0, 3) + BX, guN);
-        row6<false, false>(fld(S0, 3) - BX, guS);
-        row6<false, false>(fld(Sm, 3), gum);
-        row6<true, false>(fld(Sp, 3), gup);
-        row6<true, true>(fld(S0, 4), gv0);
-        row6<false, false>(fld(S0, 4) + BX, gvN);
-        row6<false, true>(fld(S0, 4) - BX, gvS);
-        row6<false, false>(fld(Sm, 4), gvm);
-        row6<false, false>(fld(Sp, 4), gvp);
-        row6<false, false>(fld(Sp, 4) - BX, gvpS);
-        row6<true, true>(fld(S0, 5), gw0);
-        row6<false, false>(fld(S0, 5) + BX, gwN);
-        row6<false, false>(fld(S0, 5) - BX, gwS);
-        row6<false, true>(fld(Sm, 5), gwm);
-        row6<false, false>(fld(Sm, 5) + BX, gwmN);
-        row6<false, false>(fld(Sp, 5), gwp);
-        row6<true, true>(fld(S0, 0), u0);
-        row6<true, false>(fld(S0, 0) + BX, uN);
-        row6<true, false>(fld(Sp, 0), up);
-        row6<false, true>(fld(S0, 1), v0);
-        row6<false, false>(fld(S0, 1) + BX, vN);
-        row6<false, true>(fld(S0, 1) - BX, vS);
-        row6<false, false>(fld(Sp, 1), vp);
-        row6<false, false>(fld(Sp, 1) - BX, vpS);
-        row6<false, true>(fld(S0, 2), w0);
-        row6<false, false>(fld(S0, 2) + BX, wN);
-        row6<false, true>(fld(Sm, 2), wm);
-        row6<false, false>(fld(Sm, 2) + BX, wmN);
-        row6<false, false>(fld(Sp, 2), wp);
+        int issued = 0;
+        if (tid == 0)
+            for (; issued < kSS && issued < nseq; ++issued) issue(issued, kb - 1 + issued);
 
-        float ru[4], rv[4], rw[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int C = m + 1, W = m, E = m + 2;
-            const float su_c = gu0[C], su_e = gu0[E], su_w = gu0[W], su_n = guN[C], su_s = guS[C], su_nw = guN[W];
-            const float su_km = gum[C], su_kp = gup[C], su_kp_w = gup[W];
-            const float sv_c = gv0[C], sv_e = gv0[E], sv_w = gv0[W], sv_n = gvN[C], sv_s = gvS[C], sv_se = gvS[E];
-            const float sv_km = gvm[C], sv_kp = gvp[C], sv_kp_s = gvpS[C];
-            const float sw_c = gw0[C], sw_e = gw0[E], sw_w = gw0[W], sw_n = gwN[C], sw_s = gwS[C];
-            const float sw_km = gwm[C], sw_km_e = gwm[E], sw_km_n = gwmN[C], sw_kp = gwp[C];
-            const float u_c = u0[C], u_e = u0[E], u_w = u0[W], u_n = uN[C], u_nw = uN[W];
-            const float u_kp = up[C], u_kp_w = up[W];
-            const float v_c = v0[C], v_e = v0[E], v_n = vN[C], v_s = vS[C], v_se = vS[E];
-            const float v_kp = vp[C], v_kp_s = vpS[C];
-            const float w_c = w0[C], w_e = w0[E], w_n = wN[C];
-            const float w_kmc = wm[C], w_kme = wm[E], w_kmn = wmN[C], w_kp = wp[C];
-            float r_u = tcx * ((u_e + u_c + u_c) * su_e + u_w * su_c - (u_w + u_c + u_c) * su_w - u_e * su_c);
-            r_u += tcy * ((v_c + v_e) * su_n - (v_s + v_se) * su_s);
-            r_u += tz1p * (w_c + w_e) * su_kp - tz2m * (w_kmc + w_kme) * su_km;
-            r_u += tcx * (v_c * sv_e + v_s * sv_se - v_e * sv_c - v_se * sv_s);
-            r_u += tcx * (w_c * sw_e + w_kmc * sw_km_e - w_e * sw_c - w_kme * sw_km);
-            float r_v = tcy * ((v_n + v_c + v_c) * sv_n + v_s * sv_c - (v_s + v_c + v_c) * sv_s - v_n * sv_c);
-            r_v += tcx * ((u_c + u_n) * sv_e - (u_w + u_nw) * sv_w);
-            r_v += tz1p * (w_c + w_n) * sv_kp - tz2m * (w_kmc + w_kmn) * sv_km;
-            r_v += tcy * (u_c * su_n + u_w * su_nw - u_n * su_c - u_nw * su_w);
-            r_v += tcy * (w_c * sw_n + w_kmc * sw_km_n - w_n * sw_c - w_kmn * sw_km);
-            float r_w = tz1p * (u_c * su_kp + u_w * su_kp_w) - tz20 * (u_kp * su_c + u_kp_w * su_w);
-            r_w += tz1p * (v_c * sv_kp + v_s * sv_kp_s) - tz20 * (v_kp * sv_c + v_kp_s * sv_s);
-            r_w += tcx * ((u_c + u_kp) * sw_e - (u_w + u_kp_w) * sw_w);
-            r_w += tcy * ((v_c + v_kp) * sw_n - (v_s + v_kp_s) * sw_s);
-            r_w += td1p * (w_kp + w_c + w_c) * sw_kp + td10 * w_kmc * sw_c;
-            r_w -= td2m * (w_kmc + w_c + w_c) * sw_km + td20 * w_kp * sw_c;
-            ru[m] = r_u;
-            rv[m] = r_v;
-            rw[m] = r_w;
+        const int cc = (ty + 1) * BX + 4 + kCells * tq;  // box index of the strip's first cell
+        const float tcx = (float)a.tcx, tcy = (float)a.tcy;
+        float* __restrict__ gu = static_cast<float*>(a.gu);
+        float* __restrict__ gv = static_cast<float*>(a.gv);
+        float* __restrict__ gw = static_cast<float*>(a.gw);
+        size_t g = (size_t)j * (size_t)a.sy + (size_t)(long long)i0 + (size_t)kb * (size_t)a.sz;
+
+        bool bad = false;
+        for (int q = 0; q < 3 && q < nseq; ++q) {
+            const bool ok = wait(q);
+            bad |= !ok;
+            if (ok) zero_outside_strip<NT>(stage_of(q), kb - 1 + q, a, X0, y0, tid);
         }
-        if (full_strip) {
-            float4* pu = reinterpret_cast<float4*>(gu + g);
-            float4* pv = reinterpret_cast<float4*>(gv + g);
-            float4* pw_ = reinterpret_cast<float4*>(gw + g);
-            float4 nu = make_float4(ru[0], ru[1], ru[2], ru[3]);
-            float4 nv = make_float4(rv[0], rv[1], rv[2], rv[3]);
-            float4 nw = make_float4(rw[0], rw[1], rw[2], rw[3]);
-            if (a.accumulate) {
-                const float4 ou = *pu, ov = *pv, ow = *pw_;
-                nu = make_float4(ou.x + nu.x, ou.y + nu.y, ou.z + nu.z, ou.w + nu.w);
-                nv = make_float4(ov.x + nv.x, ov.y + nv.y, ov.z + nv.z, ov.w + nv.w);
-                nw = make_float4(ow.x + nw.x, ow.y + nw.y, ow.z + nw.z, ow.w + nw.w);
+        level_coefs<float>(a, kb, tid, coef_s[0]);
+        bool abort = __syncthreads_or(bad);
+
+        for (int k = kb; k < ke && !abort; ++k) {
+            const int r = k - kb;
+            const double c_next = (tid < 7 && k + 1 < ke) ? level_coef(a, k + 1, tid) : 0.0;
+            if (r + 3 < nseq) {
+                const bool ok = wait(r + 3);
+                bad |= !ok;
+                if (ok) zero_outside_strip<NT>(stage_of(r + 3), k + 2, a, X0, y0, tid);
             }
-            *pu = nu;
-            *pv = nv;
-            *pw_ = nw;
-        } else if (row_act) {
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                if (i0 + m < 0 || i0 + m > nx + 1) continue;
-                const size_t gm = g + (size_t)m;
+            const unsigned char* Sm = stage_of(r);      // level k-1
+            const unsigned char* S0 = stage_of(r + 1);  // level k
+            const unsigned char* Sp = stage_of(r + 2);  // level k+1
+            auto fld = [&](const unsigned char* st, int f) {
+                return reinterpret_cast<const float*>(st + f * StripShape::BOX_STRIDE) + cc;
+            };
+            const float* cs = coef_s[r & 1];
+            const float tz1p = cs[0], tz2m = cs[1], tz20 = cs[2], td1p = cs[3], td10 = cs[4], td2m = cs[5], td20 = cs[6];
+
+            // rows: 0 = the strip's row, N = +1, S = -1; index m+1 = cell m,
+            // m = its west neighbour, m+2 = its east neighbour
+            float gu0[kCells + 2], guN[kCells + 2], guS[kCells + 2], gum[kCells + 2], gup[kCells + 2];
+            float gv0[kCells + 2], gvN[kCells + 2], gvS[kCells + 2], gvm[kCells + 2], gvp[kCells + 2], gvpS[kCells + 2];
+            float gw0[kCells + 2], gwN[kCells + 2], gwS[kCells + 2], gwm[kCells + 2], gwmN[kCells + 2], gwp[kCells + 2];
+            float u0[kCells + 2], uN[kCells + 2], up[kCells + 2], v0[kCells + 2], vN[kCells + 2], vS[kCells + 2];
+            float vp[kCells + 2], vpS[kCells + 2], w0[kCells + 2], wN[kCells + 2], wm[kCells + 2], wmN[kCells + 2];
+            float wp[kCells + 2];
+            row_strip<kCells, true, true>(fld(S0, 3), gu0);
+            row_strip<kCells, true, false>(fld(S0, 3) + BX, guN);
+            row_strip<kCells, false, false>(fld(S0, 3) - BX, guS);
+            row_strip<kCells, false, false>(fld(Sm, 3), gum);
+            row_strip<kCells, true, false>(fld(Sp, 3), gup);
+            row_strip<kCells, true, true>(fld(S0, 4), gv0);
+            row_strip<kCells, false, false>(fld(S0, 4) + BX, gvN);
+            row_strip<kCells, false, true>(fld(S0, 4) - BX, gvS);
+            row_strip<kCells, false, false>(fld(Sm, 4), gvm);
+            row_strip<kCells, false, false>(fld(Sp, 4), gvp);
+            row_strip<kCells, false, false>(fld(Sp, 4) - BX, gvpS);
+            row_strip<kCells, true, true>(fld(S0, 5), gw0);
+            row_strip<kCells, false, false>(fld(S0, 5) + BX, gwN);
+            row_strip<kCells, false, false>(fld(S0, 5) - BX, gwS);
+            row_strip<kCells, false, true>(fld(Sm, 5), gwm);
+            row_strip<kCells, false, false>(fld(Sm, 5) + BX, gwmN);
+            row_strip<kCells, false, false>(fld(Sp, 5), gwp);
+            row_strip<kCells, true, true>(fld(S0, 0), u0);
+            row_strip<kCells, true, false>(fld(S0, 0) + BX, uN);
+            row_strip<kCells, true, false>(fld(Sp, 0), up);
+            row_strip<kCells, false, true>(fld(S0, 1), v0);
+            row_strip<kCells, false, false>(fld(S0, 1) + BX, vN);
+            row_strip<kCells, false, true>(fld(S0, 1) - BX, vS);
+            row_strip<kCells, false, false>(fld(Sp, 1), vp);
+            row_strip<kCells, false, false>(fld(Sp, 1) - BX, vpS);
+            row_strip<kCells, false, true>(fld(S0, 2), w0);
+            row_strip<kCells, false, false>(fld(S0, 2) + BX, wN);
+            row_strip<kCells, false, true>(fld(Sm, 2), wm);
+            row_strip<kCells, false, false>(fld(Sm, 2) + BX, wmN);
+            row_strip<kCells, false, false>(fld(Sp, 2), wp);
+
+            float ru[kCells], rv[kCells], rw[kCells];
+    #pragma unroll
+            for (int m = 0; m < kCells; ++m) {
+                const int C = m + 1, W = m, E = m + 2;
+                const float su_c = gu0[C], su_e = gu0[E], su_w = gu0[W], su_n = guN[C], su_s = guS[C], su_nw = guN[W];
+                const float su_km = gum[C], su_kp = gup[C], su_kp_w = gup[W];
+                const float sv_c = gv0[C], sv_e = gv0[E], sv_w = gv0[W], sv_n = gvN[C], sv_s = gvS[C], sv_se = gvS[E];
+                const float sv_km = gvm[C], sv_kp = gvp[C], sv_kp_s = gvpS[C];
+                const float sw_c = gw0[C], sw_e = gw0[E], sw_w = gw0[W], sw_n = gwN[C], sw_s = gwS[C];
+                const float sw_km = gwm[C], sw_km_e = gwm[E], sw_km_n = gwmN[C], sw_kp = gwp[C];
+                const float u_c = u0[C], u_e = u0[E], u_w = u0[W], u_n = uN[C], u_nw = uN[W];
+                const float u_kp = up[C], u_kp_w = up[W];
+                const float v_c = v0[C], v_e = v0[E], v_n = vN[C], v_s = vS[C], v_se = vS[E];
+                const float v_kp = vp[C], v_kp_s = vpS[C];
+                const float w_c = w0[C], w_e = w0[E], w_n = wN[C];
+                const float w_kmc = wm[C], w_kme = wm[E], w_kmn = wmN[C], w_kp = wp[C];
+                float r_u = tcx * ((u_e + u_c + u_c) * su_e + u_w * su_c - (u_w + u_c + u_c) * su_w - u_e * su_c);
+                r_u += tcy * ((v_c + v_e) * su_n - (v_s + v_se) * su_s);
+                r_u += tz1p * (w_c + w_e) * su_kp - tz2m * (w_kmc + w_kme) * su_km;
+                r_u += tcx * (v_c * sv_e + v_s * sv_se - v_e * sv_c - v_se * sv_s);
+                r_u += tcx * (w_c * sw_e + w_kmc * sw_km_e - w_e * sw_c - w_kme * sw_km);
+                float r_v = tcy * ((v_n + v_c + v_c) * sv_n + v_s * sv_c - (v_s + v_c + v_c) * sv_s - v_n * sv_c);
+                r_v += tcx * ((u_c + u_n) * sv_e - (u_w + u_nw) * sv_w);
+                r_v += tz1p * (w_c + w_n) * sv_kp - tz2m * (w_kmc + w_kmn) * sv_km;
+                r_v += tcy * (u_c * su_n + u_w * su_nw - u_n * su_c - u_nw * su_w);
+                r_v += tcy * (w_c * sw_n + w_kmc * sw_km_n - w_n * sw_c - w_kmn * sw_km);
+                float r_w = tz1p * (u_c * su_kp + u_w * su_kp_w) - tz20 * (u_kp * su_c + u_kp_w * su_w);
+                r_w += tz1p * (v_c * sv_kp + v_s * sv_kp_s) - tz20 * (v_kp * sv_c + v_kp_s * sv_s);
+                r_w += tcx * ((u_c + u_kp) * sw_e - (u_w + u_kp_w) * sw_w);
+                r_w += tcy * ((v_c + v_kp) * sw_n - (v_s + v_kp_s) * sw_s);
+                r_w += td1p * (w_kp + w_c + w_c) * sw_kp + td10 * w_kmc * sw_c;
+                r_w -= td2m * (w_kmc + w_c + w_c) * sw_km + td20 * w_kp * sw_c;
+                ru[m] = r_u;
+                rv[m] = r_v;
+                rw[m] = r_w;
+            }
+            if (full_strip && kCells == 4) {
+                float4* pu = reinterpret_cast<float4*>(gu + g);
+                float4* pv = reinterpret_cast<float4*>(gv + g);
+                float4* pw_ = reinterpret_cast<float4*>(gw + g);
+                float4 nu = make_float4(ru[0], ru[1], ru[kCells - 2], ru[kCells - 1]);
+                float4 nv = make_float4(rv[0], rv[1], rv[kCells - 2], rv[kCells - 1]);
+                float4 nw = make_float4(rw[0], rw[1], rw[kCells - 2], rw[kCells - 1]);
                 if (a.accumulate) {
-                    gu[gm] += ru[m];
-                    gv[gm] += rv[m];
-                    gw[gm] += rw[m];
-                } else {
-                    gu[gm] = ru[m];
-                    gv[gm] = rv[m];
-                    gw[gm] = rw[m];
+                    const float4 ou = *pu, ov = *pv, ow = *pw_;
+                    nu = make_float4(ou.x + nu.x, ou.y + nu.y, ou.z + nu.z, ou.w + nu.w);
+                    nv = make_float4(ov.x + nv.x, ov.y + nv.y, ov.z + nv.z, ov.w + nv.w);
+                    nw = make_float4(ow.x + nw.x, ow.y + nw.y, ow.z + nw.z, ow.w + nw.w);
+                }
+                *pu = nu;
+                *pv = nv;
+                *pw_ = nw;
+            } else if (full_strip) {
+                float2* pu = reinterpret_cast<float2*>(gu + g);
+                float2* pv = reinterpret_cast<float2*>(gv + g);
+                float2* pw_ = reinterpret_cast<float2*>(gw + g);
+                float2 nu = make_float2(ru[0], ru[kCells - 1]);
+                float2 nv = make_float2(rv[0], rv[kCells - 1]);
+                float2 nw = make_float2(rw[0], rw[kCells - 1]);
+                if (a.accumulate) {
+                    const float2 ou = *pu, ov = *pv, ow = *pw_;
+                    nu = make_float2(ou.x + nu.x, ou.y + nu.y);
+                    nv = make_float2(ov.x + nv.x, ov.y + nv.y);
+                    nw = make_float2(ow.x + nw.x, ow.y + nw.y);
+                }
+                *pu = nu;
+                *pv = nv;
+                *pw_ = nw;
+            } else if (row_act) {
+    #pragma unroll
+                for (int m = 0; m < kCells; ++m) {
+                    if (i0 + m < 0 || i0 + m > nx + 1) continue;
+                    const size_t gm = g + (size_t)m;
+                    if (a.accumulate) {
+                        gu[gm] += ru[m];
+                        gv[gm] += rv[m];
+                        gw[gm] += rw[m];
+                    } else {
+                        gu[gm] = ru[m];
+                        gv[gm] = rv[m];
+                        gw[gm] = rw[m];
+                    }
                 }
             }
+            g += (size_t)a.sz;
+            if (tid < 7 && k + 1 < ke) coef_s[(r + 1) & 1][tid] = (float)c_next;
+            abort = __syncthreads_or(bad);  // level k-1's stage is free
+            if (!abort && tid == 0 && issued < nseq) {
+                fence_proxy_async_smem();
+                issue(issued, kb - 1 + issued);
+                ++issued;
+            }
         }
-        g += (size_t)a.sz;
-        if (tid < 7 && k + 1 < ke) coef_s[(r + 1) & 1][tid] = (float)c_next;
-        abort = __syncthreads_or(bad);  // level k-1's stage is free
-        if (!abort && tid == 0 && issued < nseq) {
-            fence_proxy_async_smem();
-            issue(issued, kb - 1 + issued);
-            ++issued;
+        if (abort) {
+            if (tid == 0) {
+                atomicOr(&tu_status, kStatusTimeout);
+                for (int q = (issued > kSS ? issued - kSS : 0); q < issued; ++q) (void)wait(q);
+            }
+            return;
         }
-    }
-    if (abort && tid == 0) {
-        atomicOr(&tu_status, kStatusTimeout);
-        for (int q = (issued > kSS ? issued - kSS : 0); q < issued; ++q) (void)wait(q);
+        seq0 += nseq;
     }
 }
 
@@ -706,16 +795,30 @@ TileShape adjoint_shape(int elem_bytes) {
 cudaError_t launch_adjoint(const CUtensorMap* maps6, const AdjArgs& a, cudaStream_t st) {
     AdjMaps m;
     for (int f = 0; f < kFields; ++f) m.m[f] = maps6[f];
-    // strips of four cells, tiles laid out in tensor x = i + xoff
+    // strips of kStripCells cells, tiles laid out in tensor x = i + xoff
     const int sx = (a.nx + 2 + a.xoff + kSTX - 1) / kSTX, sy = (a.ny + 2 + kSTY - 1) / kSTY;
-    cudaError_t e = cudaFuncSetAttribute(adjoint_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         StripShape::SMEM_BYTES);
+    auto kern = adjoint_strip_kernel<kStripCells>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, StripShape::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    int chunks = 1;
-    if ((e = choose_kchunks(adjoint_strip_kernel, kSNT, StripShape::SMEM_BYTES, (long long)sx * sy, a.nz,
-                            &chunks)) != cudaSuccess)
-        return e;
-    adjoint_strip_kernel<<<dim3(sx, sy, chunks), kSNT, StripShape::SMEM_BYTES, st>>>(m, a);
+    StripSched sch;
+    sch.tiles_x = sx;
+    sch.total = (long long)sx * sy * a.nz;
+    const long long tiles = (long long)sx * sy;
+    long long slots = 0;
+    if ((e = persistent_grid(kern, kSNT, StripShape::SMEM_BYTES, 1ll << 40, &slots)) != cudaSuccess) return e;
+    long long grid;
+    if (tiles >= slots) {  // chunk-major items, as many chunks as fill the waves best
+        int chunks = 1;
+        if ((e = choose_kchunks(kern, kSNT, StripShape::SMEM_BYTES, tiles, a.nz, &chunks)) != cudaSuccess) return e;
+        sch.chunks = chunks;
+        sch.len = 0;
+        grid = tiles * chunks;
+    } else {  // one wave of resident CTAs, each an equal run of units
+        sch.chunks = 0;
+        sch.len = (sch.total + slots - 1) / slots;
+        grid = (sch.total + sch.len - 1) / sch.len;
+    }
+    kern<<<(unsigned)grid, kSNT, StripShape::SMEM_BYTES, st>>>(m, a, sch);
     return cudaGetLastError();
 }
 
