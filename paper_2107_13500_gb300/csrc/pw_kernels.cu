@@ -140,7 +140,8 @@ __device__ __forceinline__ float double_to_float_rn(double d) {
 
 // Cell n (row-major over the (ny+2) x (nx+2) cells, halo included) of the
 // perturbation output's level k: the band sums' scratch slots.
-__device__ __forceinline__ float* sum_slot(float* fp, long long psy, long long psz, int nx, int k, int n) {
+template <typename F>
+__device__ __forceinline__ F* sum_slot(F* fp, long long psy, long long psz, int nx, int k, int n) {
     const int w = nx + 2, r = n / w, c = n - r * w;
     return fp + (size_t)k * (size_t)psz + (size_t)r * (size_t)psy + c;
 }
@@ -206,16 +207,15 @@ __global__ void __launch_bounds__(kSumThreads)
                         const float* __restrict__ fp, long long psy, long long psz, double* __restrict__ mean) {
     __shared__ double warp_part64[kSumThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    float* slots = const_cast<float*>(fp);
     for (int k = blockIdx.x; k < nz; k += gridDim.x) {
         bool ok = true;
-        for (int b = tid; b < nbands; b += kSumThreads) ok &= __float_as_int(*sum_slot(slots, psy, psz, nx, k, 3 * b + 2)) != 0;
+        for (int b = tid; b < nbands; b += kSumThreads) ok &= __float_as_int(*sum_slot(fp, psy, psz, nx, k, 3 * b + 2)) != 0;
         if (__syncthreads_and(ok)) {
             if (warp == 0) {
                 // lane l adds bands l, l+32, ... in order, then a fixed tree
                 pf t = {0.0f, 0.0f};
                 for (int b = lane; b < nbands; b += 32)
-                    t = padd(t, pf{*sum_slot(slots, psy, psz, nx, k, 3 * b), *sum_slot(slots, psy, psz, nx, k, 3 * b + 1)});
+                    t = padd(t, pf{*sum_slot(fp, psy, psz, nx, k, 3 * b), *sum_slot(fp, psy, psz, nx, k, 3 * b + 1)});
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     const pf u = {__shfl_xor_sync(0xffffffffu, t.h, o), __shfl_xor_sync(0xffffffffu, t.l, o)};
