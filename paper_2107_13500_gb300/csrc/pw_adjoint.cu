@@ -524,24 +524,6 @@ __device__ __forceinline__ void row_strip(const float* p, float* v) {
     }
 }
 
-// The work of a launch as (tile, level) units, tile-major (tile t's levels
-// 0..nz-1 are units t*nz .. t*nz+nz-1), handed to CTAs in one of two ways:
-//   chunks > 0: CTA b takes level chunk b / tiles of tile b % tiles (the
-//     column cut into `chunks` equal chunks, every tile's first chunk first),
-//     so the CTAs in flight read the same levels of neighbouring tiles and
-//     share their halo rows in L2 -- for domains with at least as many tiles
-//     as resident CTAs;
-//   chunks == 0: CTA b takes the run of `len` units from b * len, the end of
-//     one tile's column and the start of the next (or several whole
-//     columns), so that one wave of resident CTAs does equal work however
-//     few the tiles -- for small domains, where uniform chunks leave a
-//     partial second wave.
-struct StripSched {
-    int tiles_x;      // tiles per row of the tile grid
-    int chunks;       // level chunks per tile, or 0 for runs
-    long long total;  // tiles * nz
-    long long len;    // units per CTA (runs)
-};
 
 template <int kCells>
 __global__ void __launch_bounds__(StripThreads<kCells>::NT, kSMinBlocks)
@@ -569,20 +551,11 @@ __global__ void __launch_bounds__(StripThreads<kCells>::NT, kSMinBlocks)
     __syncthreads();
     int seq0 = 0;  // loads of this CTA's earlier tiles (all issued and consumed)
     long long unit, unit_end;
-    if (sch.chunks > 0) {
-        const long long tiles = sch.total / nz;
-        const long long c = (long long)blockIdx.x / tiles, t = (long long)blockIdx.x - c * tiles;
-        unit = t * nz + (long long)nz * c / sch.chunks;
-        unit_end = t * nz + (long long)nz * (c + 1) / sch.chunks;
-    } else {
-        unit = (long long)blockIdx.x * sch.len;
-        unit_end = unit + sch.len < sch.total ? unit + sch.len : sch.total;
-    }
+    strip_units(sch, nz, blockIdx.x, &unit, &unit_end);
     while (unit < unit_end) {
-        const long long t = unit / nz;
-        const int kb = (int)(unit - t * nz);
-        const int ke = (int)(unit_end - t * nz < nz ? unit_end - t * nz : nz);
-        unit = t * nz + ke;
+        long long t;
+        int kb, ke;
+        unit = strip_segment(unit, unit_end, nz, &t, &kb, &ke);
         const int X0 = (int)(t % sch.tiles_x) * kSTX, y0 = (int)(t / sch.tiles_x) * kSTY;
         const int i0 = X0 + kCells * tq - a.xoff;  // the strip's first cell (halo included: 0..nx+1)
         const int j = y0 + ty;
@@ -800,25 +773,15 @@ cudaError_t launch_adjoint(const CUtensorMap* maps6, const AdjArgs& a, cudaStrea
     auto kern = adjoint_strip_kernel<kStripCells>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, StripShape::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    StripSched sch;
-    sch.tiles_x = sx;
-    sch.total = (long long)sx * sy * a.nz;
     const long long tiles = (long long)sx * sy;
     long long slots = 0;
     if ((e = persistent_grid(kern, kSNT, StripShape::SMEM_BYTES, 1ll << 40, &slots)) != cudaSuccess) return e;
-    long long grid;
-    if (tiles >= slots) {  // chunk-major items, as many chunks as fill the waves best
-        int chunks = 1;
-        if ((e = choose_kchunks(kern, kSNT, StripShape::SMEM_BYTES, tiles, a.nz, &chunks)) != cudaSuccess) return e;
-        sch.chunks = chunks;
-        sch.len = 0;
-        grid = tiles * chunks;
-    } else {  // one wave of resident CTAs, each an equal run of units
-        sch.chunks = 0;
-        sch.len = (sch.total + slots - 1) / slots;
-        grid = (sch.total + sch.len - 1) / sch.len;
-    }
-    kern<<<(unsigned)grid, kSNT, StripShape::SMEM_BYTES, st>>>(m, a, sch);
+    int chunks = 1;  // chunk-major items when the tiles fill the slots, as many chunks as fill the waves best
+    if (tiles >= slots &&
+        (e = choose_kchunks(kern, kSNT, StripShape::SMEM_BYTES, tiles, a.nz, &chunks)) != cudaSuccess)
+        return e;
+    const StripSched sch = make_strip_sched(sx, tiles, a.nz, slots, chunks);
+    kern<<<(unsigned)sch.grid, kSNT, StripShape::SMEM_BYTES, st>>>(m, a, sch);
     return cudaGetLastError();
 }
 

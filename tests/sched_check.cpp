@@ -1,9 +1,12 @@
-// Host check of the one-shot launch schedule (pw_internal.h): for many tile
-// grids, level counts and slot counts, every (tile, level) of the launch is
+// Host check of the launch schedules (pw_internal.h): for many tile grids,
+// level counts and slot counts, every (tile, level) of a one-shot launch is
 // computed by exactly one work item, and every item has a valid tile and a
-// non-empty level range; and the grouped greedy model (greedy_makespan)
-// equals a direct simulation that places items one at a time on a priority
-// queue of slot loads. Prints "cases N bad M".
+// non-empty level range; the grouped greedy model (greedy_makespan) equals a
+// direct simulation that places items one at a time on a priority queue of
+// slot loads; and the strip adjoint's schedule (equal runs of tile levels,
+// or chunk-major level chunks) covers every (tile, level) exactly once with
+// non-empty segments, runs taking one wave (at most `slots` CTAs, each at
+// most ceil(units / slots) units). Prints "cases N bad M".
 #include <cmath>
 #include <cstdio>
 #include <functional>
@@ -51,6 +54,36 @@ int main() {
         if (std::fabs(pw::greedy_makespan(na, la, nb, lb, slots) - top) > 1e-9) ++bad;
         ++cases;
     }
+    // the strip adjoint's schedule
+    for (int tx : {1, 2, 9, 17, 33})
+        for (int ty : {1, 3, 17, 65})
+            for (int nz : {1, 2, 5, 37, 64, 128})
+                for (long long slots : {1LL, 7LL, 456LL, 912LL})
+                    for (int chunks : {1, 3, 5}) {
+                        const long long tiles = (long long)tx * ty;
+                        const pw::StripSched s = pw::make_strip_sched(tx, tiles, nz, slots, chunks);
+                        std::vector<int> cover((size_t)tiles * nz, 0);
+                        if (s.chunks == 0 && (s.grid > slots || s.len > (s.total + slots - 1) / slots)) ++bad;
+                        for (long long b = 0; b < s.grid; ++b) {
+                            long long u, u1;
+                            pw::strip_units(s, nz, b, &u, &u1);
+                            if (u >= u1) ++bad;  // every CTA has work
+                            while (u < u1) {
+                                long long t;
+                                int kb, ke;
+                                const long long next = pw::strip_segment(u, u1, nz, &t, &kb, &ke);
+                                if (t < 0 || t >= tiles || kb < 0 || ke > nz || kb >= ke || next <= u) {
+                                    ++bad;
+                                    break;
+                                }
+                                for (int k = kb; k < ke; ++k) cover[(size_t)t * nz + k]++;
+                                u = next;
+                            }
+                        }
+                        for (int c : cover)
+                            if (c != 1) ++bad;
+                        ++cases;
+                    }
     std::printf("cases %lld bad %lld\n", cases, bad);
     return bad != 0;
 }
