@@ -14,10 +14,11 @@
 // columns and rows, level 1, and level nz for sw) count as zero, so output
 // cells include the halo: gu, gv, gw are defined on every cell the forward
 // map reads. Threads own cells (the paired kernel two, the FP32 kernel a
-// strip of four) and march k with a TMA ring of the six fields (u, v, w,
-// gsu, gsv, gsw) -- no atomics, one write per cell. A launch splits the
-// columns into k-chunks (blockIdx.z) so that small domains still fill the
-// GPU; a chunk of output levels kb..ke-1 reads levels kb-1..ke.
+// strip of two or four) and march k with a TMA ring of the six fields (u, v,
+// w, gsu, gsv, gsw) -- no atomics, one write per cell. A launch splits the
+// columns into k-chunks so that small domains still fill the GPU (the FP32
+// kernel hands small domains out as equal runs of tile levels instead); a
+// chunk of output levels kb..ke-1 reads levels kb-1..ke.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -424,14 +425,16 @@ __global__ void fold_halo_x_kernel(T* f, int nx, int ny, int nz, long long sy, l
 
 // ---------------------------------------------------------------------------
 // FP32 adjoint on strips (PW_F32): the cell-by-cell gather, with each
-// thread owning four consecutive cells along x. Tiles are laid out in the
-// TMA tensor's x coordinate X = i + xoff (the descriptor starts at the
-// 16-byte boundary at or below i = 0), so a strip's first cell sits at a
-// multiple of four floats both in the staged box and in global memory:
-// every shared read of a neighbour row is one 16-byte load (three cover
-// the six columns i-1 .. i+4 a strip needs) and interior strips store their
-// gradients with one 16-byte store per field. A cell reads about 12 such
-// loads instead of 43 scalar ones.
+// thread owning kStripCells (two or four) consecutive cells along x. Tiles
+// are laid out in the TMA tensor's x coordinate X = i + xoff (the descriptor
+// starts at the 16-byte boundary at or below i = 0), so a strip's first cell
+// sits at a multiple of the strip's width both in the staged box and in
+// global memory: a strip of four reads the six columns i-1 .. i+4 of a
+// neighbour row with three 16-byte loads and stores each gradient with one
+// 16-byte store; a strip of two reads i-1 .. i+2 with one 8-byte and two
+// 4-byte loads and stores 8 bytes. Two cells per thread (the default) give
+// 256-thread CTAs on the same staged boxes: twice the warps per SM to hide
+// the level march's latency, for about a fifth more instructions per cell.
 
 #ifndef PW_ADJ_STRIP_TY
 #define PW_ADJ_STRIP_TY 16
