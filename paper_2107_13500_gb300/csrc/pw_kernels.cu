@@ -55,19 +55,22 @@ cudaError_t launch_fill_halo(void* field, int elem_bytes, int nx, int ny, int nz
 }
 
 // ---------------------------------------------------------------------------
-// Per-level mean and float perturbation, in two launches, kept off the slow
-// FP64 pipe (about two FP64 lane operations per clock per SM on GB300) so
-// that both are bound by HBM.
+// Per-level mean and float perturbation, in three launches that balance
+// GB300's slow FP64 pipe (about two FP64 lane operations per clock per SM)
+// against its FP32 and integer pipes.
 //
 // split_sum_kernel: a flat grid of CTAs, one per (row band, level): the
-// interior of level k is cut into nbands bands of about kSumRows rows. Each
-// thread sums its share of a band (a fixed set of columns, rows in order) in
+// interior of level k is cut into nbands bands of at most kSumRows rows.
+// Each thread sums its share of a band (a fixed set of columns, rows in
+// order): the first kSum64Rows rows of each column in FP64, the rest in
 // paired FP32 -- each double split into a float pair by integer operations,
-// pairs added with TwoSum -- then a fixed shuffle tree per warp and the
-// warps in order; thread 0 stores the band's pair and a flag (every value
-// summable as a pair) in three cells of the perturbation output's level k,
-// which split_pert_kernel overwrites afterwards. Small CTAs over every SM
-// keep enough loads in flight to stream the field at HBM rate.
+// pairs added with TwoSum, about 20 issue slots a value -- so that the FP64
+// pipe and the FP32/integer pipes share the work; the FP64 part then joins
+// the pair. A fixed shuffle tree per warp and the warps in order follow;
+// thread 0 stores the band's pair and a flag (every pair-summed value and
+// the FP64 part within the pairs' range) in three cells of the perturbation
+// output's level k, which split_pert_kernel overwrites afterwards, so no
+// scratch memory is needed.
 //
 // split_reduce_kernel: one CTA per level adds the band sums in a fixed
 // order (lane l of the first warp the bands l, l+32, ... in turn, then a
