@@ -602,11 +602,6 @@ __global__ void __launch_bounds__(StripThreads<kCells>::NT, kSMinBlocks)
         for (int k = kb; k < ke && !abort; ++k) {
             const int r = k - kb;
             const double c_next = (tid < 7 && k + 1 < ke) ? level_coef(a, k + 1, tid) : 0.0;
-            if (r + 3 < nseq) {
-                const bool ok = wait(r + 3);
-                bad |= !ok;
-                if (ok) zero_outside_strip<NT>(stage_of(r + 3), k + 2, a, X0, y0, tid);
-            }
             const unsigned char* Sm = stage_of(r);      // level k-1
             const unsigned char* S0 = stage_of(r + 1);  // level k
             const unsigned char* Sp = stage_of(r + 2);  // level k+1
@@ -741,6 +736,14 @@ __global__ void __launch_bounds__(StripThreads<kCells>::NT, kSMinBlocks)
             }
             g += (size_t)a.sz;
             if (tid < 7 && k + 1 < ke) coef_s[(r + 1) & 1][tid] = (float)c_next;
+            // level k+2, the next step's upper level: waited for here, after
+            // this step's work, so that its copy (issued at the end of the
+            // previous step) has had the whole step to arrive
+            if (r + 3 < nseq) {
+                const bool ok = wait(r + 3);
+                bad |= !ok;
+                if (ok) zero_outside_strip<NT>(stage_of(r + 3), k + 2, a, X0, y0, tid);
+            }
             abort = __syncthreads_or(bad);  // level k-1's stage is free
             if (!abort && tid == 0 && issued < nseq) {
                 fence_proxy_async_smem();
