@@ -275,6 +275,15 @@ __global__ void __launch_bounds__(kPNT, 3) adjoint_paired_kernel(const __grid_co
             adj_convert(base + ((rc + 2) % kPS) * PSh::STAGE_BYTES, slot(rc + 2), cslot(rc + 2), k + 2, x0, y0, a,
                         tid, cp, c_pre);
             c_pre = adj_coef_for(a, k + 3, tid);
+            // the staged level is split: reissue its stage now, so that the
+            // copy of the next level overlaps this step's gather
+            abort = __syncthreads_or(bad);
+            if (abort) break;
+            if (tid == 0 && issued < nl) {
+                fence_proxy_async_smem();
+                adj_issue_p(base, full, maps, issued, kb - 1 + issued, bxs, bys);
+                ++issued;
+            }
         }
         const float4* L0 = slot(rc);
         const float4* Lp = slot(rc + 1);
@@ -377,12 +386,7 @@ __global__ void __launch_bounds__(kPNT, 3) adjoint_paired_kernel(const __grid_co
         sw_km = sw_c;
         sw_km_e = sw_e;
         sw_km_n = sw_n;
-        abort = __syncthreads_or(bad);  // publishes rc+2's pairs, frees rc's slot and rc+2's stage
-        if (!abort && tid == 0 && issued < nl) {
-            fence_proxy_async_smem();
-            adj_issue_p(base, full, maps, issued, kb - 1 + issued, bxs, bys);
-            ++issued;
-        }
+        abort = __syncthreads_or(bad);  // publishes rc+2's pairs, frees rc's slot
     }
     if (abort && tid == 0) {
         atomicOr(&tu_status, kStatusTimeout);

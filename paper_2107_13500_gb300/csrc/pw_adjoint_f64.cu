@@ -453,18 +453,20 @@ __device__ __forceinline__ void adjoint_tile(const AdjF64Maps& maps, const AdjAr
                 issue(issued);
                 ++issued;
             }
-            if (!abort && cleaned < nseq) {  // level k+3, first read by the next step's scale phase
-                const bool ok = sm.wait(cleaned);
-                bad |= !ok;
-                if (ok) clean_stage(sm.stage(cleaned), kb - 1 + cleaned, a, x0, y0, tid);
-                ++cleaned;
-            }
             // ---- items of level k+1 (loads r+2, r+3)
             if (!abort) {
                 items_level<kEq>(sm, r + 2, k + 1, a, tid);
                 const double* s = sm.scl + ((k + 1) & 1) * AF::NSCALE;
                 b3c = s[b3_off<kEq>() + xi];
                 b6c = s[b6_off<kEq>() + yi];
+            }
+            // level k+3, first read by the next step's scale phase: waited for
+            // after the items phase, so that its copy (issued above) overlaps it
+            if (!abort && cleaned < nseq) {
+                const bool ok = sm.wait(cleaned);
+                bad |= !ok;
+                if (ok) clean_stage(sm.stage(cleaned), kb - 1 + cleaned, a, x0, y0, tid);
+                ++cleaned;
             }
             abort = __syncthreads_or(bad);
         }
