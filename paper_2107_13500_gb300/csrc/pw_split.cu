@@ -59,7 +59,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-template <class Cfg>
+// kLowBits: stage and phase from the low 32 bits of the load count (needs a
+// power-of-two S). The one-shot kernel takes it (two registers fewer); in
+// the persistent kernel it made the compiler spill, so that one keeps the
+// 64-bit form.
+template <class Cfg, bool kLowBits = false>
 struct SplitRing {
     unsigned char* base;
     uint64_t* full;
@@ -76,17 +80,28 @@ struct SplitRing {
         for (int s = 0; s < Cfg::S; ++s) mbar_init(&full[s], 1);
         fence_mbar_init();
     }
+    // Stage (n % S) and phase ((n / S) & 1) of load n. With a power-of-two
+    // S both follow from the low 32 bits of n, so no 64-bit arithmetic is
+    // needed for them.
+    static constexpr bool kPow2 = kLowBits && (Cfg::S & (Cfg::S - 1)) == 0;
+    static __device__ __forceinline__ int stage_of(long long seq) {
+        if constexpr (kPow2) return (int)((unsigned)seq & (unsigned)(Cfg::S - 1));
+        else return (int)(seq % Cfg::S);
+    }
+    static __device__ __forceinline__ uint32_t phase_of(long long seq) {
+        if constexpr (kPow2) return ((unsigned)seq / (unsigned)Cfg::S) & 1u;
+        else return (uint32_t)((seq / Cfg::S) & 1);
+    }
     __device__ __forceinline__ const float* box(long long seq, int f) const {
-        return reinterpret_cast<const float*>(base + (int)(seq % Cfg::S) * Cfg::STAGE_BYTES +
-                                              f * Cfg::Shape::BOX_STRIDE);
+        return reinterpret_cast<const float*>(base + stage_of(seq) * Cfg::STAGE_BYTES + f * Cfg::Shape::BOX_STRIDE);
     }
     __device__ __forceinline__ const float* row(long long seq) const {
-        return rows + (int)(seq % Cfg::S) * PW_SPLIT_NCOEF;
+        return rows + stage_of(seq) * PW_SPLIT_NCOEF;
     }
     // load number `seq` = level `lev` of the tile at (x0, y0)
     __device__ __forceinline__ void issue(long long seq, int lev, const CUtensorMap* mu, const CUtensorMap* mv,
                                           const CUtensorMap* mw, const float* table, int x0, int y0) {
-        const int s = (int)(seq % Cfg::S);
+        const int s = stage_of(seq);
         uint64_t* bar = &full[s];
         unsigned char* dst = base + s * Cfg::STAGE_BYTES;
         mbar_arrive_expect_tx(bar, 3 * Cfg::Shape::BOX_BYTES + kRowBytes);
@@ -96,7 +111,7 @@ struct SplitRing {
         bulk_load(rows + s * PW_SPLIT_NCOEF, table + (size_t)lev * PW_SPLIT_NCOEF, kRowBytes, bar);
     }
     __device__ __forceinline__ bool wait(long long seq) {
-        return mbar_wait_bounded(&full[(int)(seq % Cfg::S)], (uint32_t)((seq / Cfg::S) & 1));
+        return mbar_wait_bounded(&full[stage_of(seq)], phase_of(seq));
     }
 };
 
@@ -133,8 +148,8 @@ __device__ __forceinline__ void st4(float* g, const float* v, int n) {
 // running load count (CTA-uniform); loads are numbered relative to the
 // lowest level read, lo. Returns false if a bounded wait expired (status
 // set, in-flight loads drained).
-template <class Cfg, bool kVec>
-__device__ bool split_tile(SplitRing<Cfg>& ring, const CUtensorMap* mu, const CUtensorMap* mv,
+template <class Cfg, bool kVec, bool kLowBits>
+__device__ bool split_tile(SplitRing<Cfg, kLowBits>& ring, const CUtensorMap* mu, const CUtensorMap* mv,
                            const CUtensorMap* mw, const FwdArgs& a, int bx, int by, int kb, int ke, long long& seq,
                            int tid) {
     constexpr int S = Cfg::S, BX = Cfg::BX, TXP = Cfg::TXP, TY = Cfg::TY;
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS) fwd_split_kernel(con
                                                             const __grid_constant__ CUtensorMap mw,
                                                             const FwdArgs a, const ItemSched sched) {
     extern __shared__ unsigned char smem_raw[];
-    SplitRing<Cfg> ring;
+    SplitRing<Cfg, true> ring;
     ring.setup(smem_raw);
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -327,7 +342,7 @@ __global__ void __launch_bounds__(Cfg::NT, Cfg::MIN_BLOCKS) fwd_split_kernel(con
     long long seq = 0;
     int bx, by, k0, k1;
     sched_item(sched, a.kend - a.kbeg, blockIdx.x, &bx, &by, &k0, &k1);
-    (void)split_tile<Cfg, kVec>(ring, &mu, &mv, &mw, a, bx, by, a.kbeg + k0, a.kbeg + k1, seq, tid);
+    (void)split_tile<Cfg, kVec, true>(ring, &mu, &mv, &mw, a, bx, by, a.kbeg + k0, a.kbeg + k1, seq, tid);
 }
 
 // Persistent form: the CTA takes work items (one k-chunk of one tile of one
@@ -353,7 +368,7 @@ __device__ __forceinline__ void run_items(BatchPlan* plan, SplitRing<Cfg>& ring,
         const int ch = (int)(t / tiles), tt = (int)(t % tiles);
         const int kb = (int)((long long)args.nz * ch / kchunks);
         const int ke = (int)((long long)args.nz * (ch + 1) / kchunks);
-        if (!split_tile<Cfg, kVec>(ring, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid))
+        if (!split_tile<Cfg, kVec, false>(ring, &d.mu, &d.mv, &d.mw, args, tt % tiles_x, tt / tiles_x, kb, ke, seq, tid))
             break;
     }
 }
