@@ -26,6 +26,7 @@
 #include "pw_internal.h"
 #include "pw_pair.cuh"
 #include "pw_ring.cuh"
+#include "pw_strip_sched.h"
 
 namespace pw {
 

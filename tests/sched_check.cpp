@@ -1,4 +1,4 @@
-// Host check of the launch schedules (pw_internal.h): for many tile grids,
+// Host check of the launch schedules (pw_internal.h, pw_strip_sched.h): for many tile grids,
 // level counts and slot counts, every (tile, level) of a one-shot launch is
 // computed by exactly one work item, and every item has a valid tile and a
 // non-empty level range; the grouped greedy model (greedy_makespan) equals a
@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "pw_internal.h"
+#include "pw_strip_sched.h"
 
 int main() {
     long long bad = 0, cases = 0;
