@@ -442,7 +442,7 @@ __global__ void fold_halo_x_kernel(T* f, int nx, int ny, int nz, long long sy, l
 // the level march's latency, for about a fifth more instructions per cell.
 
 #ifndef PW_ADJ_STRIP_TY
-#define PW_ADJ_STRIP_TY 16
+#define PW_ADJ_STRIP_TY 12
 #endif
 #ifndef PW_ADJ_STRIP_STAGES
 #define PW_ADJ_STRIP_STAGES 4
